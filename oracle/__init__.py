@@ -1,0 +1,251 @@
+"""Independent CPU oracle for the primal hybrid FEM path (arXiv 2509.11133).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import or run
+anything here.  The CUDA library never does, and this package imports nothing
+from it.  The arithmetic lives in ``ph_oracle.c`` (plain C, binary128 per
+element; see its header); this module marshals arguments with ctypes and uses
+library primitives only for the global solve (numpy / scipy).
+
+Functions and the passage each one follows:
+  faces              Section 3.3 (FacesUp), jump/T+ convention of Section 2.2
+  multipliers        RFaces restriction, Listing SchurComplement_vectorization
+  csr_pattern        sparsity of sum_T P_T' S(T) P_T (Algorithm 1, assembly)
+  face_centroids     Listing StiffMassPH (Ct = (P1+P2+P3)/3)
+  tet_local          Eqs. K(T), M(T), C(T); Eq. schur; Algorithm 1 first loop
+  tet_matrices       Eqs. K(T), M(T), C(T) and the load rule of Section 4.3
+  assemble           Algorithm 1 assembly + b_D (Section 4.3)
+  solve              Eq. schur, S Lambda = rhs (a library sparse/dense solve)
+  recover            Algorithm 1 second loop
+  element_blocks     Eq. VectorForm blocks (monolithic check)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ph_oracle.c")
+_SO = os.path.join(_HERE, "libph_oracle.so")
+_LIB = None
+_LOCK = threading.Lock()
+
+STATUS = {0: "OK", 1: "ARG", 2: "DEGENERATE", 3: "NONMANIFOLD", 4: "OVERFLOW", 5: "NOMEM"}
+KIND_INTERIOR, KIND_DIRICHLET, KIND_NEUMANN = 0, 1, 2
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"oracle {where}: {STATUS.get(code, code)}")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+def build(force: bool = False) -> str:
+    """Compile ph_oracle.c into libph_oracle.so next to it (plain gcc)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            P = ctypes.c_void_p
+            I64 = ctypes.c_int64
+            D = ctypes.c_double
+            L.or_faces.argtypes = [I64, I64, P, I64, P, P, P, P, P, P]
+            L.or_multipliers.argtypes = [I64, P, P, P]
+            L.or_csr_pattern.argtypes = [I64, P, P, I64, P, P, P]
+            L.or_face_centroids.argtypes = [I64, P, P, P]
+            L.or_tet_local.argtypes = [P, D, D, P, P, P, P, P, P]
+            L.or_tet_matrices.argtypes = [P, P, P, P, P, P, P, P, P]
+            L.or_assemble.argtypes = [I64, P, P, P, I64, P, P, P, I64, P, P, P, D, P, P, P, P, P, P]
+            L.or_recover.argtypes = [I64, P, P, P, P, P, P, D, P, P, P, P]
+            L.or_element_blocks.argtypes = [I64, P, P, P, P, P, D, P, P, P, P, P]
+            for f in ("or_faces", "or_multipliers", "or_csr_pattern", "or_face_centroids", "or_tet_local",
+                      "or_tet_matrices", "or_assemble", "or_recover", "or_element_blocks"):
+                getattr(L, f).restype = ctypes.c_int
+            _LIB = L
+    return _LIB
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _check(code, where):
+    if code != 0:
+        raise OracleError(code, where)
+
+
+def faces(tet, nC, neumann=None):
+    tet = _c(tet, np.int32).reshape(-1, 4)
+    nE = tet.shape[0]
+    nb = _c(neumann if neumann is not None else np.zeros((0, 3)), np.int32).reshape(-1, 3)
+    cap = max(4 * nE, 1)
+    tet_face = np.zeros(max(4 * nE, 1), np.int32)
+    face_tet = np.zeros(2 * cap, np.int32)
+    face_vtx = np.zeros(3 * cap, np.int32)
+    face_kind = np.zeros(cap, np.int8)
+    nF = ctypes.c_int64(0)
+    _check(_lib().or_faces(nE, int(nC), _p(tet), nb.shape[0], _p(nb), _p(tet_face), _p(face_tet),
+                           _p(face_vtx), _p(face_kind), ctypes.byref(nF)), "faces")
+    n = nF.value
+    return {
+        "nF": n,
+        "tet_face": tet_face[:4 * nE].reshape(nE, 4),
+        "face_tet": face_tet[:2 * n].reshape(n, 2),
+        "face_vtx": face_vtx[:3 * n].reshape(n, 3),
+        "face_kind": face_kind[:n],
+    }
+
+
+def multipliers(face_kind):
+    fk = _c(face_kind, np.int8)
+    fm = np.zeros(max(fk.size, 1), np.int32)
+    L = ctypes.c_int64(0)
+    _check(_lib().or_multipliers(fk.size, _p(fk), _p(fm), ctypes.byref(L)), "multipliers")
+    return fm[:fk.size], L.value
+
+
+def csr_pattern(tet_face, face_mult, L):
+    tf = _c(tet_face, np.int32).reshape(-1, 4)
+    fm = _c(face_mult, np.int32)
+    nE = tf.shape[0]
+    rowptr = np.zeros(L + 1, np.int32)
+    colind = np.zeros(max(16 * nE, 1), np.int32)
+    nnz = ctypes.c_int64(0)
+    _check(_lib().or_csr_pattern(nE, _p(tf), _p(fm), int(L), _p(rowptr), _p(colind), ctypes.byref(nnz)), "csr")
+    return rowptr, colind[:nnz.value].copy()
+
+
+def face_centroids(coord, face_vtx):
+    coord = _c(coord, np.float64)
+    fv = _c(face_vtx, np.int32).reshape(-1, 3)
+    out = np.zeros((fv.shape[0], 3), np.float64)
+    _check(_lib().or_face_centroids(fv.shape[0], _p(fv), _p(coord), _p(out)), "centroids")
+    return out
+
+
+def tet_local(P, a, c, f4, sigma4, kind4=(0, 0, 0, 0), g4=(0.0, 0.0, 0.0, 0.0)):
+    P = _c(P, np.float64).reshape(12)
+    f4 = _c(f4, np.float64)
+    s4 = _c(sigma4, np.int32)
+    k4 = _c(kind4, np.int32)
+    g4 = _c(g4, np.float64)
+    S = np.zeros(16)
+    g = np.zeros(4)
+    _check(_lib().or_tet_local(_p(P), float(a), float(c), _p(f4), _p(s4), _p(k4), _p(g4), _p(S), _p(g)),
+           "tet_local")
+    return S.reshape(4, 4), g
+
+
+def tet_matrices(P, f4=(0, 0, 0, 0), sigma4=(1, 1, 1, 1)):
+    P = _c(P, np.float64).reshape(12)
+    f4 = _c(f4, np.float64)
+    s4 = _c(sigma4, np.int32)
+    K, M, C = np.zeros(16), np.zeros(16), np.zeros(16)
+    area, B = np.zeros(4), np.zeros(4)
+    vol = ctypes.c_double(0)
+    _check(_lib().or_tet_matrices(_p(P), _p(f4), _p(s4), _p(K), _p(M), _p(C), _p(area), ctypes.byref(vol),
+                                  _p(B)), "tet_matrices")
+    return {"K": K.reshape(4, 4), "M": M.reshape(4, 4), "C": C.reshape(4, 4), "area": area,
+            "vol": vol.value, "B": B}
+
+
+def assemble(coord, tet, fc, csr, a, c, f_face, uD_face=None, gN_face=None):
+    """fc: output of faces(); csr: dict with face_mult, L, rowptr, colind."""
+    coord = _c(coord, np.float64)
+    tet = _c(tet, np.int32)
+    nE = tet.shape[0]
+    rowptr, colind = csr["rowptr"], csr["colind"]
+    L = csr["L"]
+    values = np.zeros(max(colind.size, 1))
+    rhs = np.zeros(max(L, 1))
+    rhs_abs = np.zeros(max(L, 1))
+    a = _c(a, np.float64)
+    f_face = _c(f_face, np.float64)
+    uD = None if uD_face is None else _c(uD_face, np.float64)
+    gN = None if gN_face is None else _c(gN_face, np.float64)
+    _check(_lib().or_assemble(nE, _p(coord), _p(tet), _p(_c(fc["tet_face"], np.int32)), fc["nF"],
+                              _p(_c(fc["face_kind"], np.int8)), _p(_c(csr["face_mult"], np.int32)),
+                              _p(_c(fc["face_vtx"], np.int32)), L, _p(rowptr), _p(colind), _p(a), float(c),
+                              _p(f_face), _p(uD), _p(gN), _p(values), _p(rhs), _p(rhs_abs)), "assemble")
+    return values[:colind.size], rhs[:L], rhs_abs[:L]
+
+
+def recover(coord, tet, fc, face_mult, a, c, f_face, lam, gN_face=None):
+    coord = _c(coord, np.float64)
+    tet = _c(tet, np.int32)
+    nE = tet.shape[0]
+    U = np.zeros((max(nE, 1), 4))
+    gN = None if gN_face is None else _c(gN_face, np.float64)
+    lam = _c(lam if len(lam) else np.zeros(1), np.float64)
+    _check(_lib().or_recover(nE, _p(coord), _p(tet), _p(_c(fc["tet_face"], np.int32)),
+                             _p(_c(fc["face_kind"], np.int8)), _p(_c(face_mult, np.int32)), _p(_c(a, np.float64)),
+                             float(c), _p(_c(f_face, np.float64)), _p(gN), _p(lam), _p(U)), "recover")
+    return U[:nE]
+
+
+def element_blocks(t, coord, tet, fc, a, c, f_face, gN_face=None):
+    A, C, B = np.zeros(16), np.zeros(16), np.zeros(4)
+    gN = None if gN_face is None else _c(gN_face, np.float64)
+    _check(_lib().or_element_blocks(int(t), _p(_c(coord, np.float64)), _p(_c(tet, np.int32)),
+                                    _p(_c(fc["tet_face"], np.int32)), _p(_c(fc["face_kind"], np.int8)),
+                                    _p(_c(a, np.float64)), float(c), _p(_c(f_face, np.float64)), _p(gN), _p(A),
+                                    _p(C), _p(B)), "element_blocks")
+    return A.reshape(4, 4), C.reshape(4, 4), B
+
+
+def solve(rowptr, colind, values, rhs):
+    """S Lambda = rhs (Eq. schur) by a library solve: dense Cholesky for small
+    systems, SuperLU otherwise."""
+    L = rhs.size
+    if L == 0:
+        return np.zeros(0)
+    if L <= 4000:
+        H = np.zeros((L, L))
+        for r in range(L):
+            H[r, colind[rowptr[r]:rowptr[r + 1]]] = values[rowptr[r]:rowptr[r + 1]]
+        import scipy.linalg as sla
+        cf = sla.cho_factor(H)
+        return sla.cho_solve(cf, rhs)
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    H = sp.csr_matrix((values, colind, rowptr), shape=(L, L)).tocsc()
+    return spla.spsolve(H, rhs)
+
+
+def pipeline(coord, tet, a, c, f_fn, uD_fn=None, gN_fn=None, neumann=None, do_solve=True):
+    """Whole path on the CPU: faces, multipliers, CSR, face data at the
+    oracle's own face centroids, assembly, solve, recovery."""
+    fc = faces(tet, coord.shape[0], neumann)
+    fm, L = multipliers(fc["face_kind"])
+    rowptr, colind = csr_pattern(fc["tet_face"], fm, L)
+    cen = face_centroids(coord, fc["face_vtx"])
+    f_face = np.asarray(f_fn(cen), dtype=np.float64)
+    uD_face = None if uD_fn is None else np.asarray(uD_fn(cen), dtype=np.float64)
+    gN_face = None if gN_fn is None else np.asarray(gN_fn(cen), dtype=np.float64)
+    csr = {"face_mult": fm, "L": L, "rowptr": rowptr, "colind": colind}
+    values, rhs, rhs_abs = assemble(coord, tet, fc, csr, a, c, f_face, uD_face, gN_face)
+    out = dict(fc=fc, csr=csr, centroids=cen, f_face=f_face, uD_face=uD_face, gN_face=gN_face,
+               values=values, rhs=rhs, rhs_abs=rhs_abs)
+    if do_solve:
+        lam = solve(rowptr, colind, values, rhs)
+        U = recover(coord, tet, fc, fm, a, c, f_face, lam, gN_face)
+        out.update(lam=lam, U=U)
+    return out
