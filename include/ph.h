@@ -1,0 +1,196 @@
+/*
+ * ph.h -- C ABI of the GB300 library for the lowest-order primal hybrid finite
+ * element method of arXiv 2509.11133 ("Vectorized 3D mesh refinement and
+ * implementation of primal hybrid FEM in MATLAB"), generalised to
+ *
+ *     -div(a grad u) + c u = f  in Omega,   u = u_D on Gamma_D,   a grad u . nu = g on Gamma_N,
+ *
+ * with a per-element coefficient a_T > 0 and a constant c > 0 (the paper has
+ * a = c = 1, Section 4 Eq. eq1).  The library runs the data-parallel path of
+ * the method on one GPU:
+ *
+ *   ph_mesh_create   face-to-tetrahedron connectivity (Section 3.3), face and
+ *                    multiplier numbering, the CSR pattern of the condensed
+ *                    face system and per-element geometry;
+ *   ph_assemble      per-element local matrices (Section 4.2), element-wise
+ *                    Schur condensation onto the face multipliers (Eq. schur,
+ *                    Algorithm 1 first loop) and scatter into CSR;
+ *   ph_solve_pcg     a Jacobi-preconditioned conjugate-gradient solve of the
+ *                    condensed system (the paper solves it with a direct
+ *                    solver; Listing SchurComplement_vectorization);
+ *   ph_recover       element recovery U(T) = A(T)^-1 (B(T) + C(T)' Lambda_T)
+ *                    (Algorithm 1 second loop).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Array arguments are DEVICE pointers of the current CUDA device, owned by the
+ *   caller.  The library keeps no reference to them after the call returns,
+ *   except that ph_mesh_create copies coord and tet into the mesh.
+ * - Ids are 0-based int32.  tet is row-major nE x 4, coord row-major nC x 3.
+ * - Local faces of T = [a b c d] are k = 0..3: [a b c], [a c d], [a d b],
+ *   [d c b] (Section 2.2).  Face k lies opposite local vertex (3, 1, 2, 0)[k].
+ * - Faces are numbered by first occurrence in (tet, local face) order
+ *   (Section 3.3, FacesUp).  The tet of the first occurrence is T+ of the face
+ *   (sigma = +1), the other one T- (sigma = -1); a boundary face has only T+.
+ * - Multipliers are the non-Neumann faces in face order (the RFaces
+ *   restriction); l(F) is the multiplier id of face F, L their number.
+ * - Sign convention: the exported system H Lambda = rhs has
+ *   H = C A^-1 C' (symmetric positive definite) and rhs = b_D - C A^-1 B,
+ *   i.e. the negatives of the paper's S and right-hand side of Eq. schur;
+ *   Lambda is the paper's.
+ * - stream is a cudaStream_t (NULL = legacy default stream).  Calls that do not
+ *   say otherwise only enqueue work on it and return.
+ * - Every entry point returns a ph_status.  Argument errors found on the host
+ *   are returned at once and nothing is enqueued.  Errors found by kernels on
+ *   device data (for example a non-positive coefficient a_T) set a status word
+ *   in the mesh, which ph_mesh_check returns.
+ */
+#ifndef PH_H
+#define PH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ph_mesh ph_mesh;
+
+typedef enum {
+  PH_OK = 0,
+  PH_ERR_ARG = 1,            /* invalid argument or invalid mesh data        */
+  PH_ERR_DEGENERATE = 2,     /* a tetrahedron with zero (or non-finite) volume */
+  PH_ERR_NONMANIFOLD = 3,    /* a face shared by more than two tetrahedra     */
+  PH_ERR_OVERFLOW = 4,       /* a count exceeds the int32 index range         */
+  PH_ERR_NOMEM = 5,          /* device allocation failed                      */
+  PH_ERR_CUDA = 6,           /* a CUDA runtime call failed                    */
+  PH_ERR_NOT_CONVERGED = 7,  /* the iterative solve hit its iteration cap     */
+  PH_ERR_TIMEOUT = 8         /* reserved for bounded device-side waits         */
+} ph_status;
+
+/* Counts of a mesh.  nnz is the number of stored entries of H. */
+typedef struct {
+  int64_t nE, nC, nF;
+  int64_t nF_interior, nF_dirichlet, nF_neumann;
+  int64_t L, nnz;
+} ph_info;
+
+/*
+ * Build a mesh: connectivity, numbering, CSR pattern and element geometry.
+ *   coord   [nC*3] float64, vertex coordinates.
+ *   tet     [nE*4] int32, vertex ids of each tetrahedron (any orientation).
+ *   neumann [nN*3] int32 vertex triples of the Neumann boundary faces (the
+ *           paper's Nb, Listing 1), or NULL with nN = 0.  Every other boundary
+ *           face is Dirichlet.
+ * Connectivity follows Section 3.3 (FacesUp) and the jump convention of
+ * Section 2.2; it is computed on the device by bucketing face keys by their
+ * smallest vertex and matching within buckets, and is bit-identical to the
+ * definition (first occurrence numbering).
+ * Synchronises `stream` (twice: to size the face and CSR arrays).
+ * Errors: PH_ERR_ARG for ids out of [0, nC), repeated vertices in a tet, a
+ * Neumann triple that is not a boundary face of the mesh or is listed twice;
+ * PH_ERR_NONMANIFOLD; PH_ERR_DEGENERATE for det = 0; PH_ERR_OVERFLOW when
+ * 4 nE + nN, nF or nnz reaches 2^31.  On error *out is NULL.
+ * Release with ph_mesh_destroy.
+ */
+ph_status ph_mesh_create(const double* coord, int64_t nC, const int32_t* tet, int64_t nE,
+                         const int32_t* neumann, int64_t nN, void* stream, ph_mesh** out);
+
+/* Free a mesh.  Its device memory is released in `stream` order. */
+ph_status ph_mesh_destroy(ph_mesh* mesh, void* stream);
+
+/* Counts of a mesh (host-side, no synchronisation). */
+ph_status ph_mesh_info(const ph_mesh* mesh, ph_info* out);
+
+/*
+ * Copy connectivity out of the mesh.  Each output may be NULL.
+ *   tet_face      [nE*4] int32: face id of local face k; bit 31 set when the
+ *                 tet is T- of that face (sigma = -1).
+ *   face_tet      [nF*2] int32: T+, T- (-1 for a boundary face).
+ *   face_vtx      [nF*3] int32: the local vertex tuple of the face in T+.
+ *   face_kind     [nF]   int8:  0 interior, 1 Dirichlet, 2 Neumann.
+ *   face_mult     [nF]   int32: multiplier id l(F), -1 for Neumann faces.
+ *   face_centroid [nF*3] float64: (P_x + P_y + P_z)/3 in face_vtx order
+ *                 (the quadrature point of the load rule, Listing StiffMassPH).
+ *   face_area     [nF]   float64: |F|.
+ */
+ph_status ph_mesh_faces(const ph_mesh* mesh, int32_t* tet_face, int32_t* face_tet, int32_t* face_vtx,
+                        int8_t* face_kind, int32_t* face_mult, double* face_centroid, double* face_area,
+                        void* stream);
+
+/*
+ * Copy the CSR pattern of H: rowptr [L+1], colind [nnz] (int32).  Row l(F)
+ * holds F and the non-Neumann faces of F's one or two tets, columns ascending
+ * (the sparsity of sum_T P_T' S(T) P_T, Listing SchurComplement_vectorization).
+ */
+ph_status ph_csr_pattern(const ph_mesh* mesh, int32_t* rowptr, int32_t* colind, void* stream);
+
+/*
+ * Assemble and condense (Section 4.2-4.3, Eq. schur, Algorithm 1 first loop).
+ *   a       [nE] float64 coefficient per element (> 0, finite).
+ *   c       reaction constant (> 0, finite; the element solve needs c > 0).
+ *   f_face  [nF] float64: f at each face centroid (face_centroid order).  The
+ *           load uses the paper's 4-point face-centroid rule
+ *           B_j = |T|/4 sum_k f(Ct_k) phi_j(Ct_k).
+ *   uD_face [nF] float64 or NULL (= 0): u_D at Dirichlet face centroids;
+ *           b_D(F) = |F| u_D(Ct_F) (Section 4.3).
+ *   gN_face [nF] float64 or NULL (= 0): g at Neumann face centroids;
+ *           LN_j = sum_k |F_k| g(Ct_k) phi_j(Ct_k).
+ *   values  [nnz] float64 out: H in the CSR pattern of ph_csr_pattern.
+ *   rhs     [L]   float64 out.
+ * Every entry of values and rhs is overwritten.  Each stored entry of H and
+ * rhs receives at most two element contributions, so the result is bitwise
+ * deterministic.  Enqueues 2 kernels; no synchronisation, no allocation.
+ * Errors: PH_ERR_ARG (host) for NULL mesh/a/f_face/values/rhs or invalid c;
+ * an element with invalid a_T is skipped and flags PH_ERR_ARG in the mesh
+ * status (ph_mesh_check).
+ */
+ph_status ph_assemble(const ph_mesh* mesh, const double* a, double c, const double* f_face,
+                      const double* uD_face, const double* gN_face, double* values, double* rhs,
+                      void* stream);
+
+/*
+ * Element recovery (Algorithm 1 second loop): U(T) = A(T)^-1 (B(T) + C(T)'
+ * Lambda_T), Lambda_T(k) = lambda[l(F_k)] and 0 on Neumann faces.
+ *   lambda [L] float64, u [nE*4] float64 out (values of u_h at the 4 vertices
+ *   of each element, broken P1).  Other arguments as in ph_assemble.
+ * Enqueues 1 kernel; no synchronisation, no allocation.
+ */
+ph_status ph_recover(const ph_mesh* mesh, const double* a, double c, const double* f_face,
+                     const double* gN_face, const double* lambda, double* u, void* stream);
+
+/*
+ * Solve H x = b for a symmetric positive definite CSR matrix (rowptr [n+1],
+ * colind [nnz], values [nnz]) by conjugate gradients with the Jacobi
+ * preconditioner, starting from x = 0, until ||r||_2 <= rtol ||b||_2 or
+ * maxit iterations.  x [n] float64 out.  iters / relres (host pointers, may
+ * be NULL) receive the iteration count and the final relative residual.
+ * Allocates 5n + O(1) doubles of workspace from the library's pool and
+ * synchronises `stream` every 8 iterations to test convergence.
+ * Errors: PH_ERR_NOT_CONVERGED when maxit is reached (x holds the last
+ * iterate); PH_ERR_ARG for a non-positive diagonal entry.
+ */
+ph_status ph_solve_pcg(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* values,
+                       const double* b, double* x, double rtol, int32_t maxit, int32_t* iters,
+                       double* relres, void* stream);
+
+/*
+ * Synchronise `stream` and return (then clear) the mesh's device status word:
+ * PH_OK or the first error a kernel recorded since the last check.
+ */
+ph_status ph_mesh_check(ph_mesh* mesh, void* stream);
+
+/* Human-readable name of a status. */
+const char* ph_status_string(ph_status s);
+
+/* Message of the last PH_ERR_CUDA / PH_ERR_NOMEM raised in this thread. */
+const char* ph_last_error_message(void);
+
+/* Number of kernels this library has launched in this process. */
+int64_t ph_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PH_H */

@@ -1,0 +1,238 @@
+"""GB300 (sm_103a) library for the data-parallel path of the lowest-order
+primal hybrid FEM of arXiv 2509.11133: face-to-tetrahedron connectivity,
+per-element local matrices, element-wise Schur condensation onto the face
+multipliers, scatter into CSR, a PCG solve and element recovery.
+
+This module is a thin ctypes binding of the C ABI in ``include/ph.h``: it
+marshals torch CUDA tensors (device pointers) and the current CUDA stream into
+the ``ph_*`` entry points, which do all of the work in CUDA kernels.  There is
+no CPU path: if ``libph.so`` has not been built (``build.build()``), importing
+the library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+PH_OK = 0
+STATUS_NAMES = {0: "PH_OK", 1: "PH_ERR_ARG", 2: "PH_ERR_DEGENERATE", 3: "PH_ERR_NONMANIFOLD",
+                4: "PH_ERR_OVERFLOW", 5: "PH_ERR_NOMEM", 6: "PH_ERR_CUDA", 7: "PH_ERR_NOT_CONVERGED",
+                8: "PH_ERR_TIMEOUT"}
+
+# Every symbol declared in include/ph.h.
+EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces", "ph_csr_pattern", "ph_assemble",
+           "ph_recover", "ph_solve_pcg", "ph_mesh_check", "ph_status_string", "ph_last_error_message",
+           "ph_launch_count")
+
+
+class PHError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        self.name = STATUS_NAMES.get(code, str(code))
+        super().__init__(f"{where}: {self.name}" + (f" ({detail})" if detail else ""))
+
+
+class ph_info(ctypes.Structure):
+    _fields_ = [("nE", ctypes.c_int64), ("nC", ctypes.c_int64), ("nF", ctypes.c_int64),
+                ("nF_interior", ctypes.c_int64), ("nF_dirichlet", ctypes.c_int64), ("nF_neumann", ctypes.c_int64),
+                ("L", ctypes.c_int64), ("nnz", ctypes.c_int64)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libph.so (built in-tree); raise if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is not built; run paper_2509_11133_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "ph_mesh_create": [P, I64, P, I64, P, I64, P, ctypes.POINTER(P)],
+        "ph_mesh_destroy": [P, P],
+        "ph_mesh_info": [P, ctypes.POINTER(ph_info)],
+        "ph_mesh_faces": [P, P, P, P, P, P, P, P, P],
+        "ph_csr_pattern": [P, P, P, P],
+        "ph_assemble": [P, P, D, P, P, P, P, P, P],
+        "ph_recover": [P, P, D, P, P, P, P, P],
+        "ph_solve_pcg": [I64, P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P],
+        "ph_mesh_check": [P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.ph_status_string.argtypes = [ctypes.c_int]
+    L.ph_status_string.restype = ctypes.c_char_p
+    L.ph_last_error_message.argtypes = []
+    L.ph_last_error_message.restype = ctypes.c_char_p
+    L.ph_launch_count.argtypes = []
+    L.ph_launch_count.restype = ctypes.c_int64
+    _LIB = L
+    return L
+
+
+def _check(code: int, where: str):
+    if code != PH_OK:
+        detail = ""
+        if code in (5, 6):
+            detail = load().ph_last_error_message().decode()
+        raise PHError(code, where, detail)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need(t, dtype, n, name):
+    if t is None:
+        raise ValueError(f"{name} is required")
+    if t.dtype != dtype or t.numel() != n:
+        raise ValueError(f"{name}: expected {dtype} with {n} elements, got {t.dtype} with {t.numel()}")
+    return t
+
+
+def ph_launch_count() -> int:
+    return int(load().ph_launch_count())
+
+
+def ph_status_string(code: int) -> str:
+    return load().ph_status_string(code).decode()
+
+
+def ph_solve_pcg(rowptr, colind, values, rhs, x=None, rtol=1e-12, maxit=20000, stream=None, check=True):
+    """Jacobi-PCG solve of H x = rhs (all CUDA tensors). Returns (x, iters, relres, status)."""
+    n = rhs.numel()
+    if x is None:
+        x = torch.empty(n, dtype=torch.float64, device=rhs.device)
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0)
+    code = load().ph_solve_pcg(n, _ptr(rowptr), _ptr(colind), _ptr(values), _ptr(rhs), _ptr(x), float(rtol),
+                               int(maxit), ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+    if check:
+        _check(code, "ph_solve_pcg")
+    return x, it.value, rr.value, code
+
+
+class Mesh:
+    """A device mesh (``ph_mesh``): connectivity, CSR pattern and geometry.
+
+    ``coord`` (nC x 3 float64) and ``tet`` (nE x 4 int32) are CUDA tensors;
+    ``neumann`` (nN x 3 int32) optional.  Methods allocate outputs with torch
+    and call the matching ``ph_*`` entry point on the current stream.
+    """
+
+    def __init__(self, coord, tet, neumann=None, stream=None):
+        L = load()
+        coord = coord.contiguous()
+        tet = tet.contiguous()
+        if coord.dtype != torch.float64 or tet.dtype != torch.int32:
+            raise ValueError("coord float64, tet int32")
+        nb = None if neumann is None or neumann.numel() == 0 else neumann.contiguous()
+        if nb is not None and nb.dtype != torch.int32:
+            raise ValueError("neumann int32")
+        h = ctypes.c_void_p()
+        self._h = None
+        _check(L.ph_mesh_create(_ptr(coord), coord.shape[0], _ptr(tet), tet.shape[0], _ptr(nb),
+                                0 if nb is None else nb.shape[0], _stream(stream), ctypes.byref(h)),
+               "ph_mesh_create")
+        self._h = h
+        self.device = coord.device
+        inf = ph_info()
+        _check(L.ph_mesh_info(h, ctypes.byref(inf)), "ph_mesh_info")
+        self.info = {f: int(getattr(inf, f)) for f, _ in ph_info._fields_}
+        self.nE, self.nC, self.nF = self.info["nE"], self.info["nC"], self.info["nF"]
+        self.L, self.nnz = self.info["L"], self.info["nnz"]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self, stream=None):
+        if self._h is not None:
+            load().ph_mesh_destroy(self._h, _stream(stream))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _empty(self, n, dtype):
+        return torch.empty(n, dtype=dtype, device=self.device)
+
+    def faces(self, stream=None):
+        nE, nF = self.nE, self.nF
+        out = {
+            "tet_face": self._empty((nE, 4), torch.int32),
+            "face_tet": self._empty((nF, 2), torch.int32),
+            "face_vtx": self._empty((nF, 3), torch.int32),
+            "face_kind": self._empty(nF, torch.int8),
+            "face_mult": self._empty(nF, torch.int32),
+            "face_centroid": self._empty((nF, 3), torch.float64),
+            "face_area": self._empty(nF, torch.float64),
+        }
+        _check(load().ph_mesh_faces(self._h, *[_ptr(out[k]) for k in ("tet_face", "face_tet", "face_vtx", "face_kind",
+                                                                      "face_mult", "face_centroid", "face_area")],
+                                    _stream(stream)), "ph_mesh_faces")
+        return out
+
+    def csr_pattern(self, stream=None):
+        rowptr = self._empty(self.L + 1, torch.int32)
+        colind = self._empty(self.nnz, torch.int32)
+        _check(load().ph_csr_pattern(self._h, _ptr(rowptr), _ptr(colind), _stream(stream)), "ph_csr_pattern")
+        return rowptr, colind
+
+    def assemble(self, a, c, f_face, uD_face=None, gN_face=None, values=None, rhs=None, stream=None):
+        _need(a, torch.float64, self.nE, "a")
+        _need(f_face, torch.float64, self.nF, "f_face")
+        if uD_face is not None:
+            _need(uD_face, torch.float64, self.nF, "uD_face")
+        if gN_face is not None:
+            _need(gN_face, torch.float64, self.nF, "gN_face")
+        values = self._empty(self.nnz, torch.float64) if values is None else _need(values, torch.float64, self.nnz,
+                                                                                    "values")
+        rhs = self._empty(self.L, torch.float64) if rhs is None else _need(rhs, torch.float64, self.L, "rhs")
+        _check(load().ph_assemble(self._h, _ptr(a), float(c), _ptr(f_face), _ptr(uD_face), _ptr(gN_face),
+                                  _ptr(values), _ptr(rhs), _stream(stream)), "ph_assemble")
+        return values, rhs
+
+    def recover(self, a, c, f_face, lam, gN_face=None, u=None, stream=None):
+        _need(a, torch.float64, self.nE, "a")
+        _need(f_face, torch.float64, self.nF, "f_face")
+        _need(lam, torch.float64, self.L, "lambda")
+        if gN_face is not None:
+            _need(gN_face, torch.float64, self.nF, "gN_face")
+        u = self._empty((self.nE, 4), torch.float64) if u is None else _need(u, torch.float64, 4 * self.nE, "u")
+        _check(load().ph_recover(self._h, _ptr(a), float(c), _ptr(f_face), _ptr(gN_face), _ptr(lam), _ptr(u),
+                                 _stream(stream)), "ph_recover")
+        return u
+
+    def check(self, stream=None):
+        _check(load().ph_mesh_check(self._h, _stream(stream)), "ph_mesh_check")
+
+
+def ph_mesh_create(coord, tet, neumann=None, stream=None) -> Mesh:
+    return Mesh(coord, tet, neumann, stream)

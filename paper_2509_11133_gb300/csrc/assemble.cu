@@ -1,0 +1,280 @@
+// Per-element local matrices, Schur condensation onto the face multipliers and
+// scatter into CSR (Section 4.2-4.3, Eq. schur, Algorithm 1 first loop), and
+// element recovery (Algorithm 1 second loop).  One thread per tetrahedron.
+//
+// Element algebra.  With A = a K + c M (Eqs. K(T), M(T)) and the constant
+// vector 1: K 1 = 0 and M 1 = |T|/4 1, and M = |T|/20 I on the complement of 1.
+// Hence, exactly,
+//     A^-1 = J / (c|T|) + Qv,   J = 1 1',
+// where Qv is the inverse of (aK + c|T|/20 I) on the complement of 1.  Writing
+// E for the 3x3 matrix with rows P_i - P_0 (i = 1..3), G_e = E E',
+// T0 = I + 1 1' (3x3) and D0 = [-1 | I] (3x4), the gradients of the barycentric
+// coordinates are E^-1 D0 and K = (|det E|/6) D0' E^-T E^-1 D0, which gives
+//     Qv = (6/|det E|) D0' (a T0 + (c/20) G_e)^-1 G_e T0^-1 D0.
+// The 3x3 matrix a T0 + (c/20) G_e has condition number ~4 for any element
+// with a >> c h^2, so this form keeps full fp64 accuracy where forming A and
+// solving with it loses ~log10(a/(c h^2)) digits.  Qv 1 = 0.
+//
+// With C(T) = diag(sigma_k |F_k|) R (Eq. C(T)) and the rows r_k = (1 - e_o(k))/3,
+// o = (3, 1, 2, 0) the vertex opposite face k, and Qf[k][m] = Qv[o(k)][o(m)]:
+//     S[k][m] = d_k d_m (1/(c|T|) + Qf[k][m]/9),            d_k = sigma_k |F_k|,
+//     g[k]    = -d_k (h'sum/(c|T|) + (Qf h')_k / 9),
+//     h'_k    = |T|/4 f(Ct_k) + |F_k| g_N(Ct_k) [k Neumann],
+// (the load B_j = sum_k h'_k/3 [j != o(k)] is the paper's face-centroid rule),
+// and recovery U(T) = A^-1 (B + C' Lambda_T) is
+//     U[o(k)] = z'sum/(c|T|) - (Qf z')_k / 3,   z'_k = h'_k + d_k Lambda_k.
+#include <math.h>
+
+#include "ph_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ int comp(int4 v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+__device__ __forceinline__ unsigned short comps(ushort4 v, int k) {
+  return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+
+// Index of (k, m), k <= m, in the packed upper triangle 00 01 02 03 11 12 13 22 23 33.
+__host__ __device__ constexpr int ut(int k, int m) {
+  return k <= m ? (k * 7 - k * k) / 2 + m : (m * 7 - m * m) / 2 + k;
+}
+
+struct Geo {
+  double g00, g01, g02, g11, g12, g22, adet, rdet;
+};
+
+__device__ __forceinline__ Geo load_geo(const double* __restrict__ geo, int64_t t) {
+  const double2* p = reinterpret_cast<const double2*>(geo + 8 * t);
+  double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+  return Geo{a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};
+}
+
+// Qf (face-indexed, packed upper triangle) times `sc`.
+__device__ __forceinline__ void face_kernel(const Geo& G, double a, double c20, double sc6, double Q[10]) {
+  const double a2 = a + a;
+  const double m00 = fma(c20, G.g00, a2), m11 = fma(c20, G.g11, a2), m22 = fma(c20, G.g22, a2);
+  const double m01 = fma(c20, G.g01, a), m02 = fma(c20, G.g02, a), m12 = fma(c20, G.g12, a);
+  double A00 = fma(m11, m22, -m12 * m12);
+  double A01 = fma(m02, m12, -m01 * m22);
+  double A02 = fma(m01, m12, -m02 * m11);
+  double A11 = fma(m00, m22, -m02 * m02);
+  double A12 = fma(m01, m02, -m00 * m12);
+  double A22 = fma(m00, m11, -m01 * m01);
+  const double detM = fma(m00, A00, fma(m01, A01, m02 * A02));
+  const double s = sc6 * G.rdet / detM;  // sc * 6/|det E| / det M
+  A00 *= s; A01 *= s; A02 *= s; A11 *= s; A12 *= s; A22 *= s;
+  // G_e T0^-1 = G_e - (G_e 1) 1' / 4
+  const double r0 = 0.25 * (G.g00 + G.g01 + G.g02);
+  const double r1 = 0.25 * (G.g01 + G.g11 + G.g12);
+  const double r2 = 0.25 * (G.g02 + G.g12 + G.g22);
+  const double t00 = G.g00 - r0, t01 = G.g01 - r0, t02 = G.g02 - r0;
+  const double t10 = G.g01 - r1, t11 = G.g11 - r1, t12 = G.g12 - r1;
+  const double t20 = G.g02 - r2, t21 = G.g12 - r2, t22 = G.g22 - r2;
+  // Y = adj(M) G_e T0^-1 (symmetric): upper triangle
+  const double y00 = fma(A00, t00, fma(A01, t10, A02 * t20));
+  const double y01 = fma(A00, t01, fma(A01, t11, A02 * t21));
+  const double y02 = fma(A00, t02, fma(A01, t12, A02 * t22));
+  const double y11 = fma(A01, t01, fma(A11, t11, A12 * t21));
+  const double y12 = fma(A01, t02, fma(A11, t12, A12 * t22));
+  const double y22 = fma(A02, t02, fma(A12, t12, A22 * t22));
+  // Qv = D0' Y D0; faces 0,1,2,3 sit opposite vertices 3,1,2,0
+  const double c0 = y00 + y01 + y02, c1 = y01 + y11 + y12, c2 = y02 + y12 + y22;
+  Q[ut(0, 0)] = y22;
+  Q[ut(0, 1)] = y02;
+  Q[ut(0, 2)] = y12;
+  Q[ut(0, 3)] = -c2;
+  Q[ut(1, 1)] = y00;
+  Q[ut(1, 2)] = y01;
+  Q[ut(1, 3)] = -c0;
+  Q[ut(2, 2)] = y11;
+  Q[ut(2, 3)] = -c1;
+  Q[ut(3, 3)] = c0 + c1 + c2;
+}
+
+__device__ __forceinline__ double neg_if(double x, bool n) { return n ? -x : x; }
+
+// Zero the entries that receive atomic contributions: rhs and the diagonal.
+__global__ void k_zero_diag(int64_t L, const int32_t* __restrict__ rowdiag, double* __restrict__ values,
+                            double* __restrict__ rhs) {
+  int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  rhs[l] = 0.0;
+  values[rowdiag[l]] = 0.0;
+}
+
+template <bool UD, bool GN>
+__global__ void __launch_bounds__(128) k_assemble(int64_t nE, const double* __restrict__ geo,
+                                                  const int4* __restrict__ tface, const int4* __restrict__ tmult,
+                                                  const int4* __restrict__ tpos, const ushort4* __restrict__ trel,
+                                                  const double* __restrict__ face_area, const double* __restrict__ a,
+                                                  double c20, double six_over_c, const double* __restrict__ f_face,
+                                                  const double* __restrict__ uD, const double* __restrict__ gN,
+                                                  double* __restrict__ values, double* __restrict__ rhs,
+                                                  unsigned* status) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nE) return;
+  const double at = __ldg(a + t);
+  if (!(at > 0.0) || !(at < INFINITY)) {
+    ph_flag(status, PH_ERR_ARG);
+    return;
+  }
+  const Geo G = load_geo(geo, t);
+  const int4 tf = __ldg(tface + t);
+  const int4 tm = __ldg(tmult + t);
+  int F[4];
+  bool neg[4];
+  double ar[4], h[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    F[k] = comp(tf, k) & PH_ID_MASK;
+    neg[k] = comp(tf, k) < 0;
+    ar[k] = __ldg(face_area + F[k]);
+  }
+  const double q4 = G.adet * (1.0 / 24.0);  // |T| / 4
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    h[k] = q4 * __ldg(f_face + F[k]);
+    if (GN && comp(tm, k) == PH_NO_MULT) h[k] = fma(ar[k], __ldg(gN + F[k]), h[k]);
+  }
+  double Q[10];
+  face_kernel(G, at, c20, 6.0 / 9.0, Q);
+  const double icT = G.rdet * six_over_c;  // 1/(c|T|)
+  const double hs = (h[0] + h[1]) + (h[2] + h[3]);
+  const double base = icT * hs;
+  const int4 tp = __ldg(tpos + t);
+  const ushort4 tr = __ldg(trel + t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int mk = comp(tm, k);
+    if (mk == PH_NO_MULT) continue;
+    const int l = mk & PH_ID_MASK;
+    const bool bnd = mk < 0;
+    // g_k = -d_k (h'sum/(c|T|) + (Qf h')_k / 9)
+    double e = base;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) e = fma(Q[ut(k, m)], h[m], e);
+    double g = neg_if(-ar[k] * e, neg[k]);
+    if (UD && bnd) g = fma(ar[k], __ldg(uD + F[k]), g);  // b_D = |F| u_D(Ct_F)
+    const int pd = comp(tp, k);
+    const double skk = (ar[k] * ar[k]) * (icT + Q[ut(k, k)]);
+    if (bnd) {
+      values[pd] = skk;
+      rhs[l] = g;
+    } else {
+      atomicAdd(values + pd, skk);
+      atomicAdd(rhs + l, g);
+    }
+    const unsigned rel = comps(tr, k);
+    int idx = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if (m == k) continue;
+      if (comp(tm, m) != PH_NO_MULT) {
+        const int off = ((int)(rel << (28 - 4 * idx))) >> 28;  // sign-extend 4 bits
+        const double skm = (ar[k] * ar[m]) * (icT + Q[ut(k, m)]);
+        values[pd + off] = neg_if(skm, neg[k] != neg[m]);
+      }
+      ++idx;
+    }
+  }
+}
+
+template <bool GN>
+__global__ void __launch_bounds__(128) k_recover(int64_t nE, const double* __restrict__ geo,
+                                                 const int4* __restrict__ tface, const int4* __restrict__ tmult,
+                                                 const double* __restrict__ face_area, const double* __restrict__ a,
+                                                 double c20, double six_over_c, const double* __restrict__ f_face,
+                                                 const double* __restrict__ gN, const double* __restrict__ lambda,
+                                                 double* __restrict__ u, unsigned* status) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nE) return;
+  const double at = __ldg(a + t);
+  if (!(at > 0.0) || !(at < INFINITY)) {
+    ph_flag(status, PH_ERR_ARG);
+    return;
+  }
+  const Geo G = load_geo(geo, t);
+  const int4 tf = __ldg(tface + t);
+  const int4 tm = __ldg(tmult + t);
+  const double q4 = G.adet * (1.0 / 24.0);
+  double z[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int F = comp(tf, k) & PH_ID_MASK;
+    const int mk = comp(tm, k);
+    const double ar = __ldg(face_area + F);
+    double zk = q4 * __ldg(f_face + F);
+    if (mk == PH_NO_MULT) {
+      if (GN) zk = fma(ar, __ldg(gN + F), zk);
+    } else {
+      zk = fma(neg_if(ar, comp(tf, k) < 0), __ldg(lambda + (mk & PH_ID_MASK)), zk);
+    }
+    z[k] = zk;
+  }
+  double Q[10];
+  face_kernel(G, at, c20, -6.0 / 3.0, Q);  // -Qf/3
+  const double icT = G.rdet * six_over_c;
+  const double zs = icT * ((z[0] + z[1]) + (z[2] + z[3]));
+  double U[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double e = zs;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) e = fma(Q[ut(k, m)], z[m], e);
+    U[k] = e;
+  }
+  // vertex j holds U of the face opposite it: j = 0,1,2,3 <- k = 3,1,2,0
+  double2* out = reinterpret_cast<double2*>(u + 4 * t);
+  out[0] = make_double2(U[3], U[1]);
+  out[1] = make_double2(U[2], U[0]);
+}
+
+bool finite_pos(double x) { return x > 0.0 && x < INFINITY; }
+
+}  // namespace
+
+using namespace ph;
+
+extern "C" ph_status ph_assemble(const ph_mesh* m, const double* a, double c, const double* f_face,
+                                 const double* uD_face, const double* gN_face, double* values, double* rhs,
+                                 void* stream) {
+  if (!m || !finite_pos(c)) return PH_ERR_ARG;
+  if (m->nE > 0 && (!a || !f_face)) return PH_ERR_ARG;
+  if ((m->nnz > 0 && !values) || (m->L > 0 && !rhs)) return PH_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m->L > 0) {
+    k_zero_diag<<<grid_for(m->L), kThreads, 0, s>>>(m->L, m->rowdiag, values, rhs);
+    cudaError_t e = launched();
+    if (e != cudaSuccess) return cuda_status(e, "k_zero_diag");
+  }
+  if (m->nE == 0) return PH_OK;
+  const double c20 = c / 20.0, six_over_c = 6.0 / c;
+  const unsigned grid = grid_for(m->nE, 128);
+#define PH_ASM(UDV, GNV)                                                                                         \
+  k_assemble<UDV, GNV><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->tpos, m->trel, m->face_area, a, \
+                                            c20, six_over_c, f_face, uD_face, gN_face, values, rhs, m->status)
+  const bool ud = uD_face != nullptr && m->nFd > 0, gn = gN_face != nullptr && m->nFn > 0;
+  if (ud && gn) PH_ASM(true, true);
+  else if (ud) PH_ASM(true, false);
+  else if (gn) PH_ASM(false, true);
+  else PH_ASM(false, false);
+#undef PH_ASM
+  return cuda_status(launched(), "k_assemble");
+}
+
+extern "C" ph_status ph_recover(const ph_mesh* m, const double* a, double c, const double* f_face,
+                                const double* gN_face, const double* lambda, double* u, void* stream) {
+  if (!m || !finite_pos(c)) return PH_ERR_ARG;
+  if (m->nE > 0 && (!a || !f_face || !u || (m->L > 0 && !lambda))) return PH_ERR_ARG;
+  if (m->nE == 0) return PH_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double c20 = c / 20.0, six_over_c = 6.0 / c;
+  const unsigned grid = grid_for(m->nE, 128);
+  if (gN_face != nullptr && m->nFn > 0)
+    k_recover<true><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->face_area, a, c20, six_over_c, f_face,
+                                         gN_face, lambda, u, m->status);
+  else
+    k_recover<false><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->face_area, a, c20, six_over_c,
+                                          f_face, gN_face, lambda, u, m->status);
+  return cuda_status(launched(), "k_recover");
+}

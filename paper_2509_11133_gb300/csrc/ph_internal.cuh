@@ -1,0 +1,79 @@
+// Internal declarations of the primal hybrid FEM library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "ph.h"
+
+// tmult encoding: multiplier id in bits 0..30, bit 31 = Dirichlet boundary
+// face; PH_NO_MULT marks a Neumann face (no multiplier).
+#define PH_NO_MULT 0x7FFFFFFF
+#define PH_BND_BIT 0x80000000u
+#define PH_ID_MASK 0x7FFFFFFF
+
+struct ph_mesh {
+  int device;
+  int64_t nE, nC, nF, nFi, nFd, nFn, L, nnz;
+  double* coord;       // nC*3
+  int4* tet;           // nE
+  int4* tface;         // nE: face id, bit 31 = sigma < 0
+  int4* tmult;         // nE: see PH_NO_MULT / PH_BND_BIT
+  int4* tpos;          // nE: CSR position of the diagonal entry of row l(F_k)
+  ushort4* trel;       // nE: 3 packed 4-bit offsets (m != k, ascending m) from tpos
+  double* geo;         // nE*8: G_e (00,01,02,11,12,22), |det|, 1/|det|
+  int2* face_tet;      // nF
+  int32_t* face_vtx;   // nF*3
+  int8_t* face_kind;   // nF
+  int32_t* face_mult;  // nF
+  double* face_area;   // nF
+  int32_t* rowptr;     // L+1
+  int32_t* colind;     // nnz
+  int32_t* rowdiag;    // L
+  unsigned int* status;  // device status word: bit s set for ph_status s
+};
+
+namespace ph {
+
+extern std::atomic<int64_t> g_launches;
+
+// Record one kernel launch and return the launch error, if any.
+inline cudaError_t launched(int n = 1) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+void set_error_message(const char* what, cudaError_t e);
+ph_status cuda_status(cudaError_t e, const char* what);
+
+// Stream-ordered allocation from the library's memory pool of `device`.
+cudaError_t alloc_bytes(void** p, size_t bytes, cudaStream_t s);
+template <class T>
+inline cudaError_t alloc(T** p, size_t n, cudaStream_t s) {
+  return alloc_bytes(reinterpret_cast<void**>(p), n * sizeof(T) + (n == 0 ? 16 : 0), s);
+}
+void free_async(void* p, cudaStream_t s);
+
+// Exclusive prefix sum of n int32 values into out (int32); the int64 total
+// is written to *d_total (device).  in and out may alias.
+ph_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* d_total, cudaStream_t s);
+
+// First error recorded in a status word (lowest code), PH_OK if none.
+inline ph_status status_from_bits(unsigned bits) {
+  for (int c = 1; c < 32; ++c)
+    if (bits & (1u << c)) return (ph_status)c;
+  return PH_OK;
+}
+
+constexpr int kThreads = 256;
+inline unsigned grid_for(int64_t n, int threads = kThreads) {
+  int64_t g = (n + threads - 1) / threads;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace ph
+
+// Record an error code in a device status word.
+__device__ __forceinline__ void ph_flag(unsigned* status, ph_status s) { atomicOr(status, 1u << (unsigned)s); }

@@ -1,0 +1,213 @@
+// Jacobi-preconditioned conjugate gradients for the condensed face system
+// H Lambda = rhs (Eq. schur; the paper solves it with MATLAB's backslash).
+// All reductions use a fixed grid and a fixed summation order, so repeated
+// solves are bitwise reproducible.
+#include <math.h>
+
+#include "ph_internal.cuh"
+
+namespace {
+
+constexpr int RT = 256;   // threads per block
+constexpr int RB = 304;   // blocks (2 x 152 SMs) for vector kernels and partial sums
+
+struct Scalars {
+  double rz, pq, alpha, beta, rr, bb;
+};
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sm[RT / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = threadIdx.x < RT / 32 ? sm[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(RT) k_pcg_init(int64_t n, const int32_t* __restrict__ rowptr,
+                                                 const int32_t* __restrict__ colind, const double* __restrict__ val,
+                                                 const double* __restrict__ b, double* __restrict__ x,
+                                                 double* __restrict__ r, double* __restrict__ p,
+                                                 double* __restrict__ dinv, double* __restrict__ part,
+                                                 unsigned* __restrict__ bad) {
+  double rz = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT) {
+    double d = 0.0;
+    for (int j = rowptr[i]; j < rowptr[i + 1]; ++j)
+      if (colind[j] == i) d = val[j];
+    if (!(d > 0.0)) atomicOr(bad, 1u);
+    const double di = d > 0.0 ? 1.0 / d : 0.0;
+    const double bi = b[i];
+    dinv[i] = di;
+    x[i] = 0.0;
+    r[i] = bi;
+    p[i] = di * bi;
+    rz = fma(bi, di * bi, rz);
+    bb = fma(bi, bi, bb);
+  }
+  rz = block_sum(rz);
+  bb = block_sum(bb);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = rz;
+    part[RB + blockIdx.x] = bb;
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_init_scalars(const double* __restrict__ part, Scalars* sc) {
+  double rz = 0.0, bb = 0.0;
+  for (int i = threadIdx.x; i < RB; i += RT) {
+    rz += part[i];
+    bb += part[RB + i];
+  }
+  rz = block_sum(rz);
+  bb = block_sum(bb);
+  if (threadIdx.x == 0) {
+    sc->rz = rz;
+    sc->bb = bb;
+    sc->rr = bb;
+  }
+}
+
+// q = H p and the partial sums of p.q
+__global__ void __launch_bounds__(RT) k_spmv_dot(int64_t n, const int32_t* __restrict__ rowptr,
+                                                 const int32_t* __restrict__ colind, const double* __restrict__ val,
+                                                 const double* __restrict__ p, double* __restrict__ q,
+                                                 double* __restrict__ part) {
+  double pq = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT) {
+    double s = 0.0;
+    for (int j = rowptr[i]; j < rowptr[i + 1]; ++j) s = fma(val[j], p[colind[j]], s);
+    q[i] = s;
+    pq = fma(p[i], s, pq);
+  }
+  pq = block_sum(pq);
+  if (threadIdx.x == 0) part[blockIdx.x] = pq;
+}
+
+__global__ void __launch_bounds__(RT) k_alpha(const double* __restrict__ part, Scalars* sc) {
+  double pq = 0.0;
+  for (int i = threadIdx.x; i < RB; i += RT) pq += part[i];
+  pq = block_sum(pq);
+  if (threadIdx.x == 0) {
+    sc->pq = pq;
+    sc->alpha = pq > 0.0 ? sc->rz / pq : 0.0;
+  }
+}
+
+// x += alpha p, r -= alpha q, partial sums of r.z (z = dinv r) and r.r
+__global__ void __launch_bounds__(RT) k_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                               const double* __restrict__ p, const double* __restrict__ q,
+                                               const double* __restrict__ dinv, const Scalars* __restrict__ sc,
+                                               double* __restrict__ part) {
+  const double alpha = sc->alpha;
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    rz = fma(ri, dinv[i] * ri, rz);
+    rr = fma(ri, ri, rr);
+  }
+  rz = block_sum(rz);
+  rr = block_sum(rr);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = rz;
+    part[RB + blockIdx.x] = rr;
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_beta(const double* __restrict__ part, Scalars* sc) {
+  double rz = 0.0, rr = 0.0;
+  for (int i = threadIdx.x; i < RB; i += RT) {
+    rz += part[i];
+    rr += part[RB + i];
+  }
+  rz = block_sum(rz);
+  rr = block_sum(rr);
+  if (threadIdx.x == 0) {
+    sc->beta = sc->rz > 0.0 ? rz / sc->rz : 0.0;
+    sc->rz = rz;
+    sc->rr = rr;
+  }
+}
+
+// p = dinv r + beta p
+__global__ void __launch_bounds__(RT) k_direction(int64_t n, double* __restrict__ p, const double* __restrict__ r,
+                                                  const double* __restrict__ dinv, const Scalars* __restrict__ sc) {
+  const double beta = sc->beta;
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT)
+    p[i] = fma(beta, p[i], dinv[i] * r[i]);
+}
+
+}  // namespace
+
+using namespace ph;
+
+extern "C" ph_status ph_solve_pcg(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* values,
+                                  const double* b, double* x, double rtol, int32_t maxit, int32_t* iters,
+                                  double* relres, void* stream) {
+  if (iters) *iters = 0;
+  if (relres) *relres = 0.0;
+  if (n < 0 || !(rtol >= 0.0) || maxit < 0) return PH_ERR_ARG;
+  if (n == 0) return PH_OK;
+  if (!rowptr || !colind || !values || !b || !x) return PH_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* work = nullptr;
+  const size_t nvec = (size_t)n;
+  // r, p, q, dinv, partial sums (2 RB), scalars, flag
+  const size_t bytes = sizeof(double) * (4 * nvec + 2 * RB) + sizeof(Scalars) + 16;
+  cudaError_t e = alloc_bytes(reinterpret_cast<void**>(&work), bytes, s);
+  if (e != cudaSuccess) return cuda_status(e, "pcg alloc");
+  double *r = work, *p = r + nvec, *q = p + nvec, *dinv = q + nvec, *part = dinv + nvec;
+  Scalars* sc = reinterpret_cast<Scalars*>(part + 2 * RB);
+  unsigned* bad = reinterpret_cast<unsigned*>(sc + 1);
+  ph_status st = PH_OK;
+  Scalars h;
+  unsigned hbad = 0;
+  int it = 0;
+  double bnorm = 0.0, res = 0.0;
+  e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) {
+    k_pcg_init<<<RB, RT, 0, s>>>(n, rowptr, colind, values, b, x, r, p, dinv, part, bad);
+    e = launched();
+  }
+  if (e == cudaSuccess) {
+    k_init_scalars<<<1, RT, 0, s>>>(part, sc);
+    e = launched();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { st = cuda_status(e, "pcg"); goto done; }
+  if (hbad) { st = PH_ERR_ARG; goto done; }
+  bnorm = sqrt(h.bb);
+  res = bnorm;
+  while (res > rtol * bnorm && it < maxit) {
+    const int batch = (maxit - it) < 8 ? (maxit - it) : 8;
+    for (int i = 0; i < batch && e == cudaSuccess; ++i) {
+      k_spmv_dot<<<RB, RT, 0, s>>>(n, rowptr, colind, values, p, q, part);
+      k_alpha<<<1, RT, 0, s>>>(part, sc);
+      k_update<<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
+      k_beta<<<1, RT, 0, s>>>(part, sc);
+      k_direction<<<RB, RT, 0, s>>>(n, p, r, dinv, sc);
+      e = launched(5);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { st = cuda_status(e, "pcg"); goto done; }
+    it += batch;
+    res = sqrt(h.rr);
+    if (h.pq <= 0.0 && res > rtol * bnorm) break;  // breakdown (H not SPD)
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = bnorm > 0.0 ? res / bnorm : 0.0;
+  if (res > rtol * bnorm) st = PH_ERR_NOT_CONVERGED;
+done:
+  free_async(work, s);
+  return st;
+}
