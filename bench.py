@@ -1,0 +1,468 @@
+#!/usr/bin/env python3
+"""Throughput of the primal hybrid FEM path on one GB300 (or N replicas).
+
+One step = the whole data-parallel path on the lognormal workload (Kuhn 3^3
+cube refined 4 levels = 3,359,232 tets, a_K = exp(N(0,1)) seed 2, c = 0.1,
+f from u = sin(pi x) sin(pi y) sin(pi z), zero Dirichlet):
+
+    ph_mesh_create  face-to-tet connectivity, numbering, CSR pattern, geometry
+    ph_assemble     local matrices + element condensation + CSR scatter
+    ph_recover      element recovery from face multipliers (seeded Lambda)
+
+The global solve is not part of the step (it is not data-parallel work of the
+path and the metric counts assembled + condensed tets).  Inputs are resident
+in HBM when timing starts; the e2e leg repeats the step through host (pinned)
+buffers with the copies inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import meshgen  # noqa: E402
+
+METRIC = "tets assembled+condensed/s"
+UNIT = "tets/s"
+WORKLOAD = "lognormal_3m"
+# smaller case of the same recipe (Kuhn 2^3 refined 4 levels, 995,328 tets;
+# working set above L2) for profiler captures
+WORKLOADS = {"lognormal_3m": (3, 4), "lognormal_1m": (2, 4)}
+L2_BYTES = 129 * 2 ** 20
+HBM_PEAK_FALLBACK = 6800.0
+# FP64 peak derived from the recipe's nominal 1.25 TFLOP/s, 152 SMs and the
+# 2070 MHz maximum SM clock: 2 FP64 instructions (DFMA, DADD or DMUL) per SM
+# per clock -> 152 * 2 * 2.07e9 = 629.3e9 FP64 operations/s.
+FP64_PEAK_GOPS = 152 * 2 * 2.070
+# FP64 operations per element in k_assemble's formulas (each fma, add, mul or
+# div counted once): condensation kernel Qf 74, load and right-hand side 30,
+# condensed entries 48.
+ASSEMBLE_OPS_PER_TET = 152
+# Method-level bytes per element of the numeric phase: coordinates, f and
+# H counted once (136 + 24 nC/nE + 24 nF/nE).
+def assemble_bytes_per_tet(nE, nC, nF):
+    return 136.0 + 24.0 * nC / nE + 24.0 * nF / nE
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def profile_traffic():
+    """DRAM bytes per k_assemble launch from the committed ncu summary, or None
+    when assemble.cu has changed since the counters were taken."""
+    prof = os.path.join(ROOT, "profiles", "k_assemble_lognormal_3m.txt")
+    src = os.path.join(ROOT, "paper_2509_11133_gb300", "csrc", "assemble.cu")
+    try:
+        kv = {}
+        for line in open(prof):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if kv.get("assemble_cu_sha256") != sha:
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def make_problem(name):
+    if name == WORKLOAD:
+        return meshgen.problem(WORKLOAD)
+    m, k = WORKLOADS[name]
+    coord, tet = meshgen.kuhn_cube(m)
+    coord, tet, _ = meshgen.refined(coord, tet, k)
+    return meshgen.Problem(name, coord, tet, meshgen.lognormal_field(tet.shape[0], 2), 0.1,
+                           lambda x: meshgen.sin_source(x, 1.0, 1.0), info={"m": m, "k": k, "seed": 2})
+
+
+def gpu_arm(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2509_11133_gb300 as ph
+    from paper_2509_11133_gb300 import build as phbuild
+
+    if not os.path.exists(phbuild.LIB):
+        phbuild.build()
+    ph.load()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+
+    t0 = time.time()
+    p = make_problem(args.workload)
+    gen_s = time.time() - t0
+    coord_h = torch.from_numpy(np.ascontiguousarray(p.coord)).pin_memory()
+    tet_h = torch.from_numpy(np.ascontiguousarray(p.tet)).pin_memory()
+    a_h = torch.from_numpy(np.ascontiguousarray(p.a)).pin_memory()
+    coord_d, tet_d, a_d = coord_h.to(dev), tet_h.to(dev), a_h.to(dev)
+
+    # face data at the face centroids (input preparation, untimed)
+    mesh = ph.Mesh(coord_d, tet_d)
+    info = dict(mesh.info)
+    cen = mesh.faces()["face_centroid"].cpu().numpy()
+    mesh.close()
+    f_h = torch.from_numpy(np.asarray(p.f(cen), np.float64)).pin_memory()
+    lam_h = torch.from_numpy(np.random.default_rng(7).standard_normal(info["L"])).pin_memory()
+    f_d, lam_d = f_h.to(dev), lam_h.to(dev)
+    nE, nF, L, nnz = info["nE"], info["nF"], info["L"], info["nnz"]
+    values = torch.empty(nnz, dtype=torch.float64, device=dev)
+    rhs = torch.empty(L, dtype=torch.float64, device=dev)
+    u = torch.empty((nE, 4), dtype=torch.float64, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        m = ph.Mesh(coord_d, tet_d)
+        if ev is not None:
+            ev[1].record(stream)
+        m.assemble(a_d, p.c, f_d, values=values, rhs=rhs)
+        if ev is not None:
+            ev[2].record(stream)
+        m.recover(a_d, p.c, f_d, lam_d, u=u)
+        if ev is not None:
+            ev[3].record(stream)
+        m.close()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    n_launch0 = ph.ph_launch_count()
+    for i in range(args.steps):
+        step(evs[i])
+        flush.zero_()          # L2 flush between timed steps (outside the event pairs)
+    torch.cuda.synchronize()
+    n_launch = ph.ph_launch_count() - n_launch0
+    barrier()
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    create_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    asm_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    rec_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    ms_per_step = float(np.mean(step_ms))
+
+    # e2e: host (pinned) inputs -> C ABI -> host outputs, copies timed
+    values_h = torch.empty(nnz, dtype=torch.float64).pin_memory()
+    rhs_h = torch.empty(L, dtype=torch.float64).pin_memory()
+    rowptr_h = torch.empty(L + 1, dtype=torch.int32).pin_memory()
+    colind_h = torch.empty(nnz, dtype=torch.int32).pin_memory()
+    u_h = torch.empty((nE, 4), dtype=torch.float64).pin_memory()
+    rowptr_d = torch.empty(L + 1, dtype=torch.int32, device=dev)
+    colind_d = torch.empty(nnz, dtype=torch.int32, device=dev)
+
+    def step_e2e():
+        coord_d.copy_(coord_h, non_blocking=True)
+        tet_d.copy_(tet_h, non_blocking=True)
+        a_d.copy_(a_h, non_blocking=True)
+        f_d.copy_(f_h, non_blocking=True)
+        lam_d.copy_(lam_h, non_blocking=True)
+        m = ph.Mesh(coord_d, tet_d)
+        ph._check(ph.load().ph_csr_pattern(m.handle, ph._ptr(rowptr_d), ph._ptr(colind_d), ph._stream()),
+                  "ph_csr_pattern")
+        m.assemble(a_d, p.c, f_d, values=values, rhs=rhs)
+        m.recover(a_d, p.c, f_d, lam_d, u=u)
+        rowptr_h.copy_(rowptr_d, non_blocking=True)
+        colind_h.copy_(colind_d, non_blocking=True)
+        values_h.copy_(values, non_blocking=True)
+        rhs_h.copy_(rhs, non_blocking=True)
+        u_h.copy_(u, non_blocking=True)
+        m.close()
+
+    h2d = 24 * p.nC + 16 * nE + 8 * nE + 8 * nF + 8 * L
+    d2h = 4 * (L + 1) + 4 * nnz + 8 * nnz + 8 * L + 32 * nE
+    for _ in range(max(1, args.warmup // 2) if not args.no_e2e else 0):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_steps = 0 if args.no_e2e else max(3, args.steps // 4)
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    barrier()
+    for i in range(e2e_steps):
+        ee[i][0].record(stream)
+        step_e2e()
+        ee[i][1].record(stream)
+        torch.cuda.synchronize()   # outputs are on the host at the end of the step
+        flush.zero_()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in ee])) if ee else float("nan")
+
+    # max over ranks
+    if world > 1:
+        t = torch.tensor([ms_per_step, e2e_ms, float(np.mean(asm_ms))], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step, e2e_ms, asm_max = (float(x) for x in t.tolist())
+    else:
+        asm_max = float(np.mean(asm_ms))
+
+    if rank != 0:
+        return None
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+    asm_s = asm_max * 1e-3
+    ops = ASSEMBLE_OPS_PER_TET * nE
+    achieved_gops = ops / asm_s / 1e9
+    traffic = profile_traffic()
+    bpt = assemble_bytes_per_tet(nE, p.nC, nF)
+    value = world * nE / (ms_per_step * 1e-3)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": args.workload,
+            "mesh": f"Kuhn {p.info['m']}^3 unit cube, {p.info['k']} levels of the paper's 1->12 refinement",
+            "nE": nE, "nC": p.nC, "nF": nF, "L": L, "nnz": nnz,
+            "a": "exp(N(0,1)) per element, seed 2", "c": p.c, "f": "(3 pi^2 + 1) sin(pi x) sin(pi y) sin(pi z)",
+            "boundary": "zero Dirichlet",
+            "step": "ph_mesh_create + ph_assemble + ph_recover (seeded Lambda)",
+            "l2": "512 MiB buffer written between timed steps (outside the step events)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        },
+        "phases_ms": {"mesh_create": float(np.mean(create_ms)), "assemble": float(np.mean(asm_ms)),
+                      "recover": float(np.mean(rec_ms))},
+        "roofline": {
+            "kernel": "k_assemble (timed as the ph_assemble call: k_zero_diag + k_assemble)",
+            "bound": "alu",
+            "achieved": achieved_gops,
+            "peak": FP64_PEAK_GOPS,
+            "unit": "G FP64-op/s",
+            "frac": achieved_gops / FP64_PEAK_GOPS,
+            "traffic": traffic,
+            "ops_per_tet": ASSEMBLE_OPS_PER_TET,
+            "peak_source": "derived: 152 SMs x 2 FP64 inst/clk x 2070 MHz (nominal FP64 1.25 TFLOP/s)",
+        },
+        "roofline_hbm": {
+            "achieved": bpt * nE / asm_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+            "frac": bpt * nE / asm_s / 1e9 / hbm_peak, "bytes_per_tet": bpt,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
+        },
+        "e2e": None if args.no_e2e else {"value": world * nE / (e2e_ms * 1e-3), "unit": UNIT,
+                                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": int(n_launch),
+        "gpu_launches_per_step": n_launch / args.steps,
+        "clocks": clk,
+        "setup": {"host_mesh_generation_s": gen_s},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, budget_s=args.cpu_budget)
+    return line
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def oracle_sample(p, n_tets):
+    """Sub-mesh of the first n_tets elements (vertices renumbered), its own
+    face data, coefficients and a seeded Lambda."""
+    tet = p.tet[:n_tets]
+    used, inv = np.unique(tet.ravel(), return_inverse=True)
+    tet_s = inv.reshape(-1, 4).astype(np.int32)
+    coord_s = p.coord[used]
+    return coord_s, tet_s, p.a[:n_tets]
+
+
+def oracle_step(p, coord_s, tet_s, a_s):
+    import oracle
+    fc = oracle.faces(tet_s, coord_s.shape[0])
+    fm, L = oracle.multipliers(fc["face_kind"])
+    rowptr, colind = oracle.csr_pattern(fc["tet_face"], fm, L)
+    cen = oracle.face_centroids(coord_s, fc["face_vtx"])
+    f = np.asarray(p.f(cen), np.float64)
+    csr = {"face_mult": fm, "L": L, "rowptr": rowptr, "colind": colind}
+    oracle.assemble(coord_s, tet_s, fc, csr, a_s, p.c, f)
+    lam = np.random.default_rng(7).standard_normal(L)
+    oracle.recover(coord_s, tet_s, fc, fm, a_s, p.c, f, lam)
+
+
+def cpu_baseline(p, budget_s=15.0, steps=1):
+    """Time the oracle as it stands (single thread) on a sample sized to
+    about budget_s seconds of CPU work."""
+    import oracle
+    oracle.build()
+    n = 2000
+    coord_s, tet_s, a_s = oracle_sample(p, n)
+    t0 = time.perf_counter()
+    oracle_step(p, coord_s, tet_s, a_s)
+    dt = time.perf_counter() - t0
+    n = int(min(p.nE, max(2000, n * budget_s / max(dt, 1e-6) / max(steps, 1))))
+    coord_s, tet_s, a_s = oracle_sample(p, n)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle_step(p, coord_s, tet_s, a_s)
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    return {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} tets of the {WORKLOAD} mesh as a sub-mesh: faces, multipliers, CSR pattern, "
+                      f"assembly+condensation (binary128 per element), recovery; {t:.2f} s per pass"}
+
+
+def reference_arm(args):
+    p = meshgen.problem(WORKLOAD)
+    import oracle
+    oracle.build()
+    # size one step to ~budget seconds, then W + K steps
+    budget = max(1.0, args.ref_step_s)
+    n = 2000
+    coord_s, tet_s, a_s = oracle_sample(p, n)
+    t0 = time.perf_counter()
+    oracle_step(p, coord_s, tet_s, a_s)
+    dt = time.perf_counter() - t0
+    n = int(min(p.nE, max(2000, n * budget / max(dt, 1e-6))))
+    coord_s, tet_s, a_s = oracle_sample(p, n)
+    for _ in range(args.warmup):
+        oracle_step(p, coord_s, tet_s, a_s)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(p, coord_s, tet_s, a_s)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = n / (ms * 1e-3)
+    sample = (f"first {n} tets of the {WORKLOAD} mesh as a sub-mesh per step: faces, multipliers, CSR pattern, "
+              f"assembly+condensation, recovery (single-threaded C oracle, binary128 per element)")
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nE_sample": n, "c": p.c},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiler runs)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-step-s", type=float, default=3.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(reference_arm(args)), flush=True)
+        return 0
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        line = gpu_arm(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
