@@ -174,6 +174,36 @@ ph_status ph_solve_pcg(int64_t n, const int32_t* rowptr, const int32_t* colind, 
                        const double* b, double* x, double rtol, int32_t maxit, int32_t* iters,
                        double* relres, void* stream);
 
+/* Largest system size n accepted by ph_solve_pcg_noalloc. */
+#define PH_PCG_NOALLOC_MAX_N 262144
+
+/*
+ * ph_solve_pcg_noalloc -- the same Jacobi-preconditioned CG as ph_solve_pcg
+ * (same arguments, same iteration, same results), but it allocates no device
+ * memory.  The paper has no counterpart to this entry point: it exists for
+ * callers that cannot allocate GPU memory while they run, for example a
+ * long-running service that reserves its whole memory budget at start-up or
+ * runs under a fixed device-memory quota, where a mid-run cudaMalloc can fail
+ * or stall.  The caller still passes the CSR matrix, b and x.
+ *
+ * Workspace: a fixed device array inside the library (about 8.4 MB: four
+ * vectors of PH_PCG_NOALLOC_MAX_N doubles plus reduction space).  Every GPU on
+ * which the library's kernels are loaded holds it until the process exits.
+ * - n > PH_PCG_NOALLOC_MAX_N is rejected with PH_ERR_ARG before any GPU work;
+ *   ph_last_error_message() then names the limit.
+ * - The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any stream
+ *   capture.
+ * - All calls share the one array, which keeps the previous call's contents
+ *   (each call re-initialises what it reads).  Calls that overlap on the GPU,
+ *   from several streams or threads, race on it: serialise them.
+ * Never calls cudaMalloc, cudaFree or any allocating routine.  Synchronises
+ * `stream` every 8 iterations, like ph_solve_pcg.
+ */
+ph_status ph_solve_pcg_noalloc(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* values,
+                               const double* b, double* x, double rtol, int32_t maxit, int32_t* iters,
+                               double* relres, void* stream);
+
 /*
  * Synchronise `stream` and return (then clear) the mesh's device status word:
  * PH_OK or the first error a kernel recorded since the last check.

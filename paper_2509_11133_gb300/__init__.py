@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "PH_OK", 1: "PH_ERR_ARG", 2: "PH_ERR_DEGENERATE", 3: "PH_ERR_
 # Every symbol declared in include/ph.h.
 EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces", "ph_csr_pattern", "ph_assemble",
            "ph_recover", "ph_solve_pcg", "ph_mesh_check", "ph_status_string", "ph_last_error_message",
-           "ph_launch_count")
+           "ph_launch_count", "ph_solve_pcg_noalloc")
 
 
 class PHError(RuntimeError):
@@ -68,6 +68,7 @@ def load(path: str | None = None):
         "ph_assemble": [P, P, D, P, P, P, P, P, P],
         "ph_recover": [P, P, D, P, P, P, P, P],
         "ph_solve_pcg": [I64, P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P],
+        "ph_solve_pcg_noalloc": [I64, P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P],
         "ph_mesh_check": [P, P],
     }
     for name, args in sig.items():
@@ -133,6 +134,24 @@ def ph_solve_pcg(rowptr, colind, values, rhs, x=None, rtol=1e-12, maxit=20000, s
     if check:
         _check(code, "ph_solve_pcg")
     return x, it.value, rr.value, code
+
+
+def ph_solve_pcg_noalloc(rowptr, colind, values, rhs, x=None, rtol=1e-12, maxit=20000, stream=None, check=True):
+    """ph_solve_pcg without device allocation inside the library (workspace in
+    a fixed device array; n <= PH_PCG_NOALLOC_MAX_N).  ``x`` is caller-owned."""
+    n = rhs.numel()
+    if x is None:
+        x = torch.empty(n, dtype=torch.float64, device=rhs.device)
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0)
+    code = load().ph_solve_pcg_noalloc(n, _ptr(rowptr), _ptr(colind), _ptr(values), _ptr(rhs), _ptr(x),
+                                       float(rtol), int(maxit), ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+    if check:
+        _check(code, "ph_solve_pcg_noalloc")
+    return x, it.value, rr.value, code
+
+
+PH_PCG_NOALLOC_MAX_N = 262144
 
 
 class Mesh:

@@ -46,6 +46,7 @@ inline cudaError_t launched(int n = 1) {
 }
 
 void set_error_message(const char* what, cudaError_t e);
+void set_error_text(const char* text);
 ph_status cuda_status(cudaError_t e, const char* what);
 
 // Stream-ordered allocation from the library's memory pool of `device`.

@@ -17,6 +17,8 @@ void set_error_message(const char* what, cudaError_t e) {
   snprintf(t_msg, sizeof t_msg, "%s: %s", what, cudaGetErrorString(e));
 }
 
+void set_error_text(const char* text) { snprintf(t_msg, sizeof t_msg, "%s", text); }
+
 ph_status cuda_status(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return PH_OK;
   set_error_message(what, e);

@@ -211,3 +211,100 @@ done:
   free_async(work, s);
   return st;
 }
+
+// ---------------------------------------------------------------------------
+// ph_solve_pcg_noalloc: the iteration above with its workspace in a fixed
+// device array instead of the library's pool, for callers that must not
+// allocate device memory.  It reuses the kernels above unchanged.
+// ---------------------------------------------------------------------------
+#include <string.h>
+
+#include <mutex>
+
+// r, p, q, dinv (4 n doubles), partial sums (2 RB), scalars and the flag word.
+static constexpr size_t kNoAllocDoubles =
+    4 * (size_t)PH_PCG_NOALLOC_MAX_N + 2 * (size_t)RB + (sizeof(Scalars) + 16 + 7) / 8;
+static __device__ __align__(256) double g_pcg_noalloc_work[kNoAllocDoubles];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[64];
+
+// Device address of g_pcg_noalloc_work on the current device, looked up once per
+// device (the host-side symbol is only a stand-in and must not reach a kernel).
+static ph_status noalloc_workspace(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e, "ph_solve_pcg_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= 64) return PH_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_pcg_noalloc_work);
+    if (e != cudaSuccess) return cuda_status(e, "ph_solve_pcg_noalloc: cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return PH_OK;
+}
+
+extern "C" ph_status ph_solve_pcg_noalloc(int64_t n, const int32_t* rowptr, const int32_t* colind,
+                                          const double* values, const double* b, double* x, double rtol,
+                                          int32_t maxit, int32_t* iters, double* relres, void* stream) {
+  if (iters) *iters = 0;
+  if (relres) *relres = 0.0;
+  if (n < 0 || !(rtol >= 0.0) || maxit < 0) return PH_ERR_ARG;
+  if (n > PH_PCG_NOALLOC_MAX_N) {
+    ph::set_error_text("ph_solve_pcg_noalloc: n exceeds PH_PCG_NOALLOC_MAX_N (the fixed workspace)");
+    return PH_ERR_ARG;
+  }
+  if (n == 0) return PH_OK;
+  if (!rowptr || !colind || !values || !b || !x) return PH_ERR_ARG;
+  double* work = nullptr;
+  ph_status st = noalloc_workspace(&work);
+  if (st != PH_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nvec = (size_t)n;
+  double *r = work, *p = r + nvec, *q = p + nvec, *dinv = q + nvec, *part = dinv + nvec;
+  Scalars* sc = reinterpret_cast<Scalars*>(part + 2 * RB);
+  unsigned* bad = reinterpret_cast<unsigned*>(sc + 1);
+  Scalars h;
+  unsigned hbad = 0;
+  int it = 0;
+  double bnorm = 0.0, res = 0.0;
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s);  // the only word that must start at zero
+  if (e == cudaSuccess) {
+    k_pcg_init<<<RB, RT, 0, s>>>(n, rowptr, colind, values, b, x, r, p, dinv, part, bad);
+    e = launched();
+  }
+  if (e == cudaSuccess) {
+    k_init_scalars<<<1, RT, 0, s>>>(part, sc);
+    e = launched();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e, "ph_solve_pcg_noalloc");
+  if (hbad) return PH_ERR_ARG;
+  bnorm = sqrt(h.bb);
+  res = bnorm;
+  while (res > rtol * bnorm && it < maxit) {
+    const int batch = (maxit - it) < 8 ? (maxit - it) : 8;
+    for (int i = 0; i < batch && e == cudaSuccess; ++i) {
+      k_spmv_dot<<<RB, RT, 0, s>>>(n, rowptr, colind, values, p, q, part);
+      k_alpha<<<1, RT, 0, s>>>(part, sc);
+      k_update<<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
+      k_beta<<<1, RT, 0, s>>>(part, sc);
+      k_direction<<<RB, RT, 0, s>>>(n, p, r, dinv, sc);
+      e = launched(5);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e, "ph_solve_pcg_noalloc");
+    it += batch;
+    res = sqrt(h.rr);
+    if (h.pq <= 0.0 && res > rtol * bnorm) break;
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = bnorm > 0.0 ? res / bnorm : 0.0;
+  return res > rtol * bnorm ? PH_ERR_NOT_CONVERGED : PH_OK;
+}
