@@ -240,10 +240,10 @@ def jitter_interior(coord, tet, frac=0.2, seed=3, min_ratio=0.1, max_rounds=12):
     disp = np.zeros_like(coord)
     idx = np.nonzero(radius > 0)[0]
     disp[idx] = draw(idx, radius[idx])
+    newc = coord + disp
+    v = _signed_vol6(newc, tet)
     redrawn = 0
     for rnd in range(max_rounds + 1):
-        newc = coord + disp
-        v = _signed_vol6(newc, tet)
         bad = ~(v / vol0 >= min_ratio)
         if not bad.any():
             return newc, redrawn
@@ -255,7 +255,12 @@ def jitter_interior(coord, tet, frac=0.2, seed=3, min_ratio=0.1, max_rounds=12):
             disp[verts] = 0.0
         else:
             disp[verts] = draw(verts, radius[verts])
-    newc = coord + disp
+        newc[verts] = coord[verts] + disp[verts]
+        # only tets touching a moved vertex change volume
+        moved = np.zeros(nC, dtype=bool)
+        moved[verts] = True
+        touched = np.nonzero(moved[tet].any(axis=1))[0]
+        v[touched] = _signed_vol6(newc, tet[touched])
     return newc, redrawn
 
 

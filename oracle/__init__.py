@@ -13,6 +13,7 @@ Functions and the passage each one follows:
   csr_pattern        sparsity of sum_T P_T' S(T) P_T (Algorithm 1, assembly)
   face_centroids     Listing StiffMassPH (Ct = (P1+P2+P3)/3)
   tet_local          Eqs. K(T), M(T), C(T); Eq. schur; Algorithm 1 first loop
+  tet_recover        Algorithm 1 second loop, one element
   tet_matrices       Eqs. K(T), M(T), C(T) and the load rule of Section 4.3
   assemble           Algorithm 1 assembly + b_D (Section 4.3)
   solve              Eq. schur, S Lambda = rhs (a library sparse/dense solve)
@@ -72,8 +73,9 @@ def _lib():
             L.or_assemble.argtypes = [I64, P, P, P, I64, P, P, P, I64, P, P, P, D, P, P, P, P, P, P]
             L.or_recover.argtypes = [I64, P, P, P, P, P, P, D, P, P, P, P]
             L.or_element_blocks.argtypes = [I64, P, P, P, P, P, D, P, P, P, P, P]
+            L.or_tet_recover.argtypes = [P, D, D, P, P, P, P, P, P]
             for f in ("or_faces", "or_multipliers", "or_csr_pattern", "or_face_centroids", "or_tet_local",
-                      "or_tet_matrices", "or_assemble", "or_recover", "or_element_blocks"):
+                      "or_tet_matrices", "or_assemble", "or_recover", "or_element_blocks", "or_tet_recover"):
                 getattr(L, f).restype = ctypes.c_int
             _LIB = L
     return _LIB
@@ -152,6 +154,15 @@ def tet_local(P, a, c, f4, sigma4, kind4=(0, 0, 0, 0), g4=(0.0, 0.0, 0.0, 0.0)):
     _check(_lib().or_tet_local(_p(P), float(a), float(c), _p(f4), _p(s4), _p(k4), _p(g4), _p(S), _p(g)),
            "tet_local")
     return S.reshape(4, 4), g
+
+
+def tet_recover(P, a, c, f4, sigma4, lam4, kind4=(0, 0, 0, 0), g4=(0.0, 0.0, 0.0, 0.0)):
+    """U = A^-1 (B + C' lam) of one element (Algorithm 1, second loop)."""
+    U = np.zeros(4)
+    _check(_lib().or_tet_recover(_p(_c(P, np.float64).reshape(12)), float(a), float(c), _p(_c(f4, np.float64)),
+                                 _p(_c(sigma4, np.int32)), _p(_c(kind4, np.int32)), _p(_c(g4, np.float64)),
+                                 _p(_c(lam4, np.float64)), _p(U)), "tet_recover")
+    return U
 
 
 def tet_matrices(P, f4=(0, 0, 0, 0), sigma4=(1, 1, 1, 1)):

@@ -8,7 +8,7 @@
  * Everything here is the paper's definitions written out, element by element:
  *   - faces: every distinct vertex set of a local face is one face, numbered
  *     by first occurrence in (tet, local face) order; the tet of the first
- *     occurrence is T+ (Section 3.3, FacesUp; Section 4.1 jump definition);
+ *     occurrence is T+ (Section 3.3, FacesUp; the jump definition of Section 2.2);
  *   - local matrices K(T), M(T), C(T) (Eqs. K(T), M(T), C(T), Section 4.2),
  *     the face-centroid load rule and b_D, LN (Section 4.3);
  *   - element condensation S(T) = C A^-1 C', rhs(T) = b_D - C A^-1 B
@@ -554,5 +554,28 @@ int or_element_blocks(int64_t t, const double* coord, const int32_t* tet, const 
     for (int j = 0; j < 4; ++j) { A16[4 * i + j] = (double)Lq.A[i][j]; C16[4 * i + j] = (double)Lq.C[i][j]; }
     B4[i] = (double)Lq.B[i];
   }
+  return OR_OK;
+}
+
+/* Recovery of one element (Algorithm 1 second loop): U = A^-1 (B + C' lam4),
+ * lam4[k] the multiplier of local face k (ignored on Neumann faces). */
+int or_tet_recover(const double* P12, double a, double c, const double* f4, const int32_t* sig4,
+                   const int32_t* kind4, const double* g4, const double* lam4, double* U4) {
+  double P[4][3];
+  for (int i = 0; i < 4; ++i)
+    for (int d = 0; d < 3; ++d) P[i][d] = P12[3 * i + d];
+  geom_q G;
+  local_q Lq;
+  if (!local_system(P, a, c, f4, sig4, kind4, g4, &G, &Lq)) return OR_ERR_DEGENERATE;
+  qf A[4][4], R[4][8];
+  memcpy(A, Lq.A, sizeof A);
+  for (int j = 0; j < 4; ++j) {
+    qf s = Lq.B[j];
+    for (int k = 0; k < 4; ++k)
+      if (kind4[k] != KIND_NEUMANN) s += Lq.C[k][j] * (qf)lam4[k];
+    R[j][0] = s;
+  }
+  if (!qsolve(4, A, 1, R)) return OR_ERR_DEGENERATE;
+  for (int j = 0; j < 4; ++j) U4[j] = (double)R[j][0];
   return OR_OK;
 }

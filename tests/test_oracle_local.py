@@ -168,3 +168,17 @@ def test_quad_accuracy_against_mpmath():
             for m_ in range(4):
                 ref = float(Sm[k, m_])
                 assert abs(S[k, m_] - ref) <= 2.3e-16 * abs(ref)
+
+
+def test_tet_recover_inverts_the_local_system():
+    """U = A^-1 (B + C' lam) satisfies A U = B + C' lam (checked with the
+    separately exported A, C, B of the same element)."""
+    rng = np.random.default_rng(21)
+    for _ in range(10):
+        P = rand_tet(rng)
+        sig = rng.choice([-1, 1], 4)
+        f, lam = rng.standard_normal(4), rng.standard_normal(4)
+        U = oracle.tet_recover(P, 1.0, 1.0, f, sig, lam)
+        m = oracle.tet_matrices(P, f, sig)
+        A = m["K"] + m["M"]
+        assert np.allclose(A @ U, m["B"] + m["C"].T @ lam, rtol=1e-12, atol=1e-14 * np.abs(A @ U).max())
