@@ -51,9 +51,9 @@ HBM_PEAK_FALLBACK = 6800.0
 # per clock -> 152 * 2 * 2.07e9 = 629.3e9 FP64 operations/s.
 FP64_PEAK_GOPS = 152 * 2 * 2.070
 # FP64 operations per element in k_assemble's formulas (each fma, add, mul or
-# div counted once): condensation kernel Qf 74, load and right-hand side 30,
-# condensed entries 48.
-ASSEMBLE_OPS_PER_TET = 152
+# div counted once): condensation kernel Qf 56, load and right-hand side 30,
+# condensed entries 30.
+ASSEMBLE_OPS_PER_TET = 116
 # Method-level bytes per element of the numeric phase: coordinates, f and
 # H counted once (136 + 24 nC/nE + 24 nF/nE).
 def assemble_bytes_per_tet(nE, nC, nF):
@@ -183,6 +183,7 @@ def gpu_arm(args, rank, world, local_rank):
     values = torch.empty(nnz, dtype=torch.float64, device=dev)
     rhs = torch.empty(L, dtype=torch.float64, device=dev)
     u = torch.empty((nE, 4), dtype=torch.float64, device=dev)
+    factor = torch.empty((nE, 10), dtype=torch.float64, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step(ev=None):
@@ -191,10 +192,10 @@ def gpu_arm(args, rank, world, local_rank):
         m = ph.Mesh(coord_d, tet_d)
         if ev is not None:
             ev[1].record(stream)
-        m.assemble(a_d, p.c, f_d, values=values, rhs=rhs)
+        m.assemble(a_d, p.c, f_d, values=values, rhs=rhs, factor=factor)
         if ev is not None:
             ev[2].record(stream)
-        m.recover(a_d, p.c, f_d, lam_d, u=u)
+        m.recover_factored(factor, p.c, f_d, lam_d, u=u)
         if ev is not None:
             ev[3].record(stream)
         m.close()
@@ -245,8 +246,8 @@ def gpu_arm(args, rank, world, local_rank):
         m = ph.Mesh(coord_d, tet_d)
         ph._check(ph.load().ph_csr_pattern(m.handle, ph._ptr(rowptr_d), ph._ptr(colind_d), ph._stream()),
                   "ph_csr_pattern")
-        m.assemble(a_d, p.c, f_d, values=values, rhs=rhs)
-        m.recover(a_d, p.c, f_d, lam_d, u=u)
+        m.assemble(a_d, p.c, f_d, values=values, rhs=rhs, factor=factor)
+        m.recover_factored(factor, p.c, f_d, lam_d, u=u)
         rowptr_h.copy_(rowptr_d, non_blocking=True)
         colind_h.copy_(colind_d, non_blocking=True)
         values_h.copy_(values, non_blocking=True)
@@ -309,7 +310,7 @@ def gpu_arm(args, rank, world, local_rank):
             "nE": nE, "nC": p.nC, "nF": nF, "L": L, "nnz": nnz,
             "a": "exp(N(0,1)) per element, seed 2", "c": p.c, "f": "(3 pi^2 + 1) sin(pi x) sin(pi y) sin(pi z)",
             "boundary": "zero Dirichlet",
-            "step": "ph_mesh_create + ph_assemble + ph_recover (seeded Lambda)",
+            "step": "ph_mesh_create + ph_assemble (with element factor) + ph_recover_factored (seeded Lambda)",
             "l2": "512 MiB buffer written between timed steps (outside the step events)",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
         },

@@ -138,6 +138,12 @@ ph_status ph_csr_pattern(const ph_mesh* mesh, int32_t* rowptr, int32_t* colind, 
  *           LN_j = sum_k |F_k| g(Ct_k) phi_j(Ct_k).
  *   values  [nnz] float64 out: H in the CSR pattern of ph_csr_pattern.
  *   rhs     [L]   float64 out.
+ *   factor  [nE*10] float64 out, or NULL: the element factor, i.e. the 10
+ *           entries (k <= m, packed 00 01 02 03 11 12 13 22 23 33) of each
+ *           element's 4x4 face-indexed block of A^-1 on the complement of the
+ *           constants, divided by 9.  ph_recover_factored reuses it instead of
+ *           recomputing the condensation; it is valid for this mesh and this
+ *           a, c only.
  * Every entry of values and rhs is overwritten.  Each stored entry of H and
  * rhs receives at most two element contributions, so the result is bitwise
  * deterministic.  Enqueues 2 kernels; no synchronisation, no allocation.
@@ -147,7 +153,7 @@ ph_status ph_csr_pattern(const ph_mesh* mesh, int32_t* rowptr, int32_t* colind, 
  */
 ph_status ph_assemble(const ph_mesh* mesh, const double* a, double c, const double* f_face,
                       const double* uD_face, const double* gN_face, double* values, double* rhs,
-                      void* stream);
+                      double* factor, void* stream);
 
 /*
  * Element recovery (Algorithm 1 second loop): U(T) = A(T)^-1 (B(T) + C(T)'
@@ -158,6 +164,15 @@ ph_status ph_assemble(const ph_mesh* mesh, const double* a, double c, const doub
  */
 ph_status ph_recover(const ph_mesh* mesh, const double* a, double c, const double* f_face,
                      const double* gN_face, const double* lambda, double* u, void* stream);
+
+/*
+ * Element recovery from the element factor written by ph_assemble (same
+ * result as ph_recover up to rounding; no condensation arithmetic is redone).
+ *   factor [nE*10] from ph_assemble on this mesh with the same a and c.
+ * Other arguments as in ph_recover.  Enqueues 1 kernel.
+ */
+ph_status ph_recover_factored(const ph_mesh* mesh, const double* factor, double c, const double* f_face,
+                              const double* gN_face, const double* lambda, double* u, void* stream);
 
 /*
  * Solve H x = b for a symmetric positive definite CSR matrix (rowptr [n+1],

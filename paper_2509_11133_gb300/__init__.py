@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "PH_OK", 1: "PH_ERR_ARG", 2: "PH_ERR_DEGENERATE", 3: "PH_ERR_
 # Every symbol declared in include/ph.h.
 EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces", "ph_csr_pattern", "ph_assemble",
            "ph_recover", "ph_solve_pcg", "ph_mesh_check", "ph_status_string", "ph_last_error_message",
-           "ph_launch_count", "ph_solve_pcg_noalloc")
+           "ph_launch_count", "ph_solve_pcg_noalloc", "ph_recover_factored")
 
 
 class PHError(RuntimeError):
@@ -65,7 +65,8 @@ def load(path: str | None = None):
         "ph_mesh_info": [P, ctypes.POINTER(ph_info)],
         "ph_mesh_faces": [P, P, P, P, P, P, P, P, P],
         "ph_csr_pattern": [P, P, P, P],
-        "ph_assemble": [P, P, D, P, P, P, P, P, P],
+        "ph_assemble": [P, P, D, P, P, P, P, P, P, P],
+        "ph_recover_factored": [P, P, D, P, P, P, P, P],
         "ph_recover": [P, P, D, P, P, P, P, P],
         "ph_solve_pcg": [I64, P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P],
         "ph_solve_pcg_noalloc": [I64, P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P],
@@ -224,7 +225,9 @@ class Mesh:
         _check(load().ph_csr_pattern(self._h, _ptr(rowptr), _ptr(colind), _stream(stream)), "ph_csr_pattern")
         return rowptr, colind
 
-    def assemble(self, a, c, f_face, uD_face=None, gN_face=None, values=None, rhs=None, stream=None):
+    def assemble(self, a, c, f_face, uD_face=None, gN_face=None, values=None, rhs=None, factor=None, stream=None):
+        """H values and rhs; with ``factor`` (nE*10 float64, or True to
+        allocate) also the element factor for recover_factored."""
         _need(a, torch.float64, self.nE, "a")
         _need(f_face, torch.float64, self.nF, "f_face")
         if uD_face is not None:
@@ -234,8 +237,14 @@ class Mesh:
         values = self._empty(self.nnz, torch.float64) if values is None else _need(values, torch.float64, self.nnz,
                                                                                     "values")
         rhs = self._empty(self.L, torch.float64) if rhs is None else _need(rhs, torch.float64, self.L, "rhs")
+        if factor is True:
+            factor = self._empty((self.nE, 10), torch.float64)
+        elif factor is not None:
+            _need(factor, torch.float64, 10 * self.nE, "factor")
         _check(load().ph_assemble(self._h, _ptr(a), float(c), _ptr(f_face), _ptr(uD_face), _ptr(gN_face),
-                                  _ptr(values), _ptr(rhs), _stream(stream)), "ph_assemble")
+                                  _ptr(values), _ptr(rhs), _ptr(factor), _stream(stream)), "ph_assemble")
+        if factor is not None:
+            return values, rhs, factor
         return values, rhs
 
     def recover(self, a, c, f_face, lam, gN_face=None, u=None, stream=None):
@@ -247,6 +256,17 @@ class Mesh:
         u = self._empty((self.nE, 4), torch.float64) if u is None else _need(u, torch.float64, 4 * self.nE, "u")
         _check(load().ph_recover(self._h, _ptr(a), float(c), _ptr(f_face), _ptr(gN_face), _ptr(lam), _ptr(u),
                                  _stream(stream)), "ph_recover")
+        return u
+
+    def recover_factored(self, factor, c, f_face, lam, gN_face=None, u=None, stream=None):
+        _need(factor, torch.float64, 10 * self.nE, "factor")
+        _need(f_face, torch.float64, self.nF, "f_face")
+        _need(lam, torch.float64, self.L, "lambda")
+        if gN_face is not None:
+            _need(gN_face, torch.float64, self.nF, "gN_face")
+        u = self._empty((self.nE, 4), torch.float64) if u is None else _need(u, torch.float64, 4 * self.nE, "u")
+        _check(load().ph_recover_factored(self._h, _ptr(factor), float(c), _ptr(f_face), _ptr(gN_face), _ptr(lam),
+                                          _ptr(u), _stream(stream)), "ph_recover_factored")
         return u
 
     def check(self, stream=None):

@@ -23,6 +23,10 @@
 // (the load B_j = sum_k h'_k/3 [j != o(k)] is the paper's face-centroid rule),
 // and recovery U(T) = A^-1 (B + C' Lambda_T) is
 //     U[o(k)] = z'sum/(c|T|) - (Qf z')_k / 3,   z'_k = h'_k + d_k Lambda_k.
+// G_e and G_e T0^-1 come precomputed per element from the mesh (they depend
+// on the geometry only).  ph_assemble can also store Qf/9 per element (the
+// "element factor", 10 numbers) so that ph_recover_factored skips the
+// condensation kernel.
 #include <math.h>
 
 #include "ph_internal.cuh"
@@ -40,16 +44,19 @@ __host__ __device__ constexpr int ut(int k, int m) {
 }
 
 struct Geo {
-  double g00, g01, g02, g11, g12, g22, adet, rdet;
+  double g00, g01, g02, g11, g12, g22;  // G_e
+  double t00, t01, t02, t10, t11, t12, t20, t21, t22;  // G_e T0^-1
+  double adet, rdet;
 };
 
 __device__ __forceinline__ Geo load_geo(const double* __restrict__ geo, int64_t t) {
-  const double2* p = reinterpret_cast<const double2*>(geo + 8 * t);
-  double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
-  return Geo{a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};
+  const double2* p = reinterpret_cast<const double2*>(geo + PH_GEO_STRIDE * t);
+  const double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3), e = __ldg(p + 4);
+  const double2 f = __ldg(p + 5), g = __ldg(p + 6), h = __ldg(p + 7), i = __ldg(p + 8);
+  return Geo{a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y, e.x, e.y, f.x, f.y, g.x, g.y, h.x, h.y, i.x};
 }
 
-// Qf (face-indexed, packed upper triangle) times `sc`.
+// Qf (face-indexed, packed upper triangle) times sc = sc6/6.
 __device__ __forceinline__ void face_kernel(const Geo& G, double a, double c20, double sc6, double Q[10]) {
   const double a2 = a + a;
   const double m00 = fma(c20, G.g00, a2), m11 = fma(c20, G.g11, a2), m22 = fma(c20, G.g22, a2);
@@ -63,20 +70,13 @@ __device__ __forceinline__ void face_kernel(const Geo& G, double a, double c20, 
   const double detM = fma(m00, A00, fma(m01, A01, m02 * A02));
   const double s = sc6 * G.rdet / detM;  // sc * 6/|det E| / det M
   A00 *= s; A01 *= s; A02 *= s; A11 *= s; A12 *= s; A22 *= s;
-  // G_e T0^-1 = G_e - (G_e 1) 1' / 4
-  const double r0 = 0.25 * (G.g00 + G.g01 + G.g02);
-  const double r1 = 0.25 * (G.g01 + G.g11 + G.g12);
-  const double r2 = 0.25 * (G.g02 + G.g12 + G.g22);
-  const double t00 = G.g00 - r0, t01 = G.g01 - r0, t02 = G.g02 - r0;
-  const double t10 = G.g01 - r1, t11 = G.g11 - r1, t12 = G.g12 - r1;
-  const double t20 = G.g02 - r2, t21 = G.g12 - r2, t22 = G.g22 - r2;
   // Y = adj(M) G_e T0^-1 (symmetric): upper triangle
-  const double y00 = fma(A00, t00, fma(A01, t10, A02 * t20));
-  const double y01 = fma(A00, t01, fma(A01, t11, A02 * t21));
-  const double y02 = fma(A00, t02, fma(A01, t12, A02 * t22));
-  const double y11 = fma(A01, t01, fma(A11, t11, A12 * t21));
-  const double y12 = fma(A01, t02, fma(A11, t12, A12 * t22));
-  const double y22 = fma(A02, t02, fma(A12, t12, A22 * t22));
+  const double y00 = fma(A00, G.t00, fma(A01, G.t10, A02 * G.t20));
+  const double y01 = fma(A00, G.t01, fma(A01, G.t11, A02 * G.t21));
+  const double y02 = fma(A00, G.t02, fma(A01, G.t12, A02 * G.t22));
+  const double y11 = fma(A01, G.t01, fma(A11, G.t11, A12 * G.t21));
+  const double y12 = fma(A01, G.t02, fma(A11, G.t12, A12 * G.t22));
+  const double y22 = fma(A02, G.t02, fma(A12, G.t12, A22 * G.t22));
   // Qv = D0' Y D0; faces 0,1,2,3 sit opposite vertices 3,1,2,0
   const double c0 = y00 + y01 + y02, c1 = y01 + y11 + y12, c2 = y02 + y12 + y22;
   Q[ut(0, 0)] = y22;
@@ -102,7 +102,7 @@ __global__ void k_zero_diag(int64_t L, const int32_t* __restrict__ rowdiag, doub
   values[rowdiag[l]] = 0.0;
 }
 
-template <bool UD, bool GN>
+template <bool UD, bool GN, bool FAC>
 __global__ void __launch_bounds__(128) k_assemble(int64_t nE, const double* __restrict__ geo,
                                                   const int4* __restrict__ tface, const int4* __restrict__ tmult,
                                                   const int4* __restrict__ tpos, const ushort4* __restrict__ trel,
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(128) k_assemble(int64_t nE, const double* __re
                                                   double c20, double six_over_c, const double* __restrict__ f_face,
                                                   const double* __restrict__ uD, const double* __restrict__ gN,
                                                   double* __restrict__ values, double* __restrict__ rhs,
-                                                  unsigned* status) {
+                                                  double* __restrict__ factor, unsigned* status) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nE) return;
   const double at = __ldg(a + t);
@@ -138,9 +138,23 @@ __global__ void __launch_bounds__(128) k_assemble(int64_t nE, const double* __re
   }
   double Q[10];
   face_kernel(G, at, c20, 6.0 / 9.0, Q);
+  if (FAC) {
+    double2* fo = reinterpret_cast<double2*>(factor + 10 * t);
+    fo[0] = make_double2(Q[0], Q[1]);
+    fo[1] = make_double2(Q[2], Q[3]);
+    fo[2] = make_double2(Q[4], Q[5]);
+    fo[3] = make_double2(Q[6], Q[7]);
+    fo[4] = make_double2(Q[8], Q[9]);
+  }
   const double icT = G.rdet * six_over_c;  // 1/(c|T|)
   const double hs = (h[0] + h[1]) + (h[2] + h[3]);
   const double base = icT * hs;
+  // condensed block S[k][m] = d_k d_m (1/(c|T|) + Qf/9), each entry once
+  double S[10];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int m = k; m < 4; ++m) S[ut(k, m)] = neg_if((ar[k] * ar[m]) * (icT + Q[ut(k, m)]), neg[k] != neg[m]);
   const int4 tp = __ldg(tpos + t);
   const ushort4 tr = __ldg(trel + t);
 #pragma unroll
@@ -156,12 +170,11 @@ __global__ void __launch_bounds__(128) k_assemble(int64_t nE, const double* __re
     double g = neg_if(-ar[k] * e, neg[k]);
     if (UD && bnd) g = fma(ar[k], __ldg(uD + F[k]), g);  // b_D = |F| u_D(Ct_F)
     const int pd = comp(tp, k);
-    const double skk = (ar[k] * ar[k]) * (icT + Q[ut(k, k)]);
     if (bnd) {
-      values[pd] = skk;
+      values[pd] = S[ut(k, k)];
       rhs[l] = g;
     } else {
-      atomicAdd(values + pd, skk);
+      atomicAdd(values + pd, S[ut(k, k)]);
       atomicAdd(rhs + l, g);
     }
     const unsigned rel = comps(tr, k);
@@ -171,11 +184,37 @@ __global__ void __launch_bounds__(128) k_assemble(int64_t nE, const double* __re
       if (m == k) continue;
       if (comp(tm, m) != PH_NO_MULT) {
         const int off = ((int)(rel << (28 - 4 * idx))) >> 28;  // sign-extend 4 bits
-        const double skm = (ar[k] * ar[m]) * (icT + Q[ut(k, m)]);
-        values[pd + off] = neg_if(skm, neg[k] != neg[m]);
+        values[pd + off] = S[ut(k, m)];
       }
       ++idx;
     }
+  }
+}
+
+__device__ __forceinline__ void store_u(double* __restrict__ u, int64_t t, const double U[4]) {
+  // vertex j holds U of the face opposite it: j = 0,1,2,3 <- k = 3,1,2,0
+  double2* out = reinterpret_cast<double2*>(u + 4 * t);
+  out[0] = make_double2(U[3], U[1]);
+  out[1] = make_double2(U[2], U[0]);
+}
+
+// z'_k = |T|/4 f(Ct_k) + |F_k| g(Ct_k) [Neumann] + d_k Lambda_k
+template <bool GN>
+__device__ __forceinline__ void recovery_load(double q4, int4 tf, int4 tm, const double* __restrict__ face_area,
+                                              const double* __restrict__ f_face, const double* __restrict__ gN,
+                                              const double* __restrict__ lambda, double z[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int F = comp(tf, k) & PH_ID_MASK;
+    const int mk = comp(tm, k);
+    const double ar = __ldg(face_area + F);
+    double zk = q4 * __ldg(f_face + F);
+    if (mk == PH_NO_MULT) {
+      if (GN) zk = fma(ar, __ldg(gN + F), zk);
+    } else {
+      zk = fma(neg_if(ar, comp(tf, k) < 0), __ldg(lambda + (mk & PH_ID_MASK)), zk);
+    }
+    z[k] = zk;
   }
 }
 
@@ -194,23 +233,8 @@ __global__ void __launch_bounds__(128) k_recover(int64_t nE, const double* __res
     return;
   }
   const Geo G = load_geo(geo, t);
-  const int4 tf = __ldg(tface + t);
-  const int4 tm = __ldg(tmult + t);
-  const double q4 = G.adet * (1.0 / 24.0);
   double z[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int F = comp(tf, k) & PH_ID_MASK;
-    const int mk = comp(tm, k);
-    const double ar = __ldg(face_area + F);
-    double zk = q4 * __ldg(f_face + F);
-    if (mk == PH_NO_MULT) {
-      if (GN) zk = fma(ar, __ldg(gN + F), zk);
-    } else {
-      zk = fma(neg_if(ar, comp(tf, k) < 0), __ldg(lambda + (mk & PH_ID_MASK)), zk);
-    }
-    z[k] = zk;
-  }
+  recovery_load<GN>(G.adet * (1.0 / 24.0), __ldg(tface + t), __ldg(tmult + t), face_area, f_face, gN, lambda, z);
   double Q[10];
   face_kernel(G, at, c20, -6.0 / 3.0, Q);  // -Qf/3
   const double icT = G.rdet * six_over_c;
@@ -223,10 +247,38 @@ __global__ void __launch_bounds__(128) k_recover(int64_t nE, const double* __res
     for (int m = 0; m < 4; ++m) e = fma(Q[ut(k, m)], z[m], e);
     U[k] = e;
   }
-  // vertex j holds U of the face opposite it: j = 0,1,2,3 <- k = 3,1,2,0
-  double2* out = reinterpret_cast<double2*>(u + 4 * t);
-  out[0] = make_double2(U[3], U[1]);
-  out[1] = make_double2(U[2], U[0]);
+  store_u(u, t, U);
+}
+
+// Recovery from the element factor Qf/9 stored by ph_assemble.
+template <bool GN>
+__global__ void __launch_bounds__(128) k_recover_factored(int64_t nE, const double* __restrict__ geo,
+                                                          const int4* __restrict__ tface, const int4* __restrict__ tmult,
+                                                          const double* __restrict__ face_area,
+                                                          const double* __restrict__ factor, double six_over_c,
+                                                          const double* __restrict__ f_face,
+                                                          const double* __restrict__ gN,
+                                                          const double* __restrict__ lambda, double* __restrict__ u) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nE) return;
+  const double2 dr = __ldg(reinterpret_cast<const double2*>(geo + PH_GEO_STRIDE * t) + 7);  // (t22, |det|)
+  const double rdet = __ldg(geo + PH_GEO_STRIDE * t + 16);
+  double z[4];
+  recovery_load<GN>(dr.y * (1.0 / 24.0), __ldg(tface + t), __ldg(tmult + t), face_area, f_face, gN, lambda, z);
+  const double2* fp = reinterpret_cast<const double2*>(factor + 10 * t);
+  const double2 q0 = __ldg(fp), q1 = __ldg(fp + 1), q2 = __ldg(fp + 2), q3 = __ldg(fp + 3), q4 = __ldg(fp + 4);
+  const double Q[10] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y, q3.x, q3.y, q4.x, q4.y};
+  const double icT = rdet * six_over_c;
+  const double zs = icT * ((z[0] + z[1]) + (z[2] + z[3]));
+  double U[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double e = 0.0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) e = fma(Q[ut(k, m)], z[m], e);
+    U[k] = fma(-3.0, e, zs);  // U[o(k)] = z'sum/(c|T|) - 3 (Qf/9 z')_k
+  }
+  store_u(u, t, U);
 }
 
 bool finite_pos(double x) { return x > 0.0 && x < INFINITY; }
@@ -237,7 +289,7 @@ using namespace ph;
 
 extern "C" ph_status ph_assemble(const ph_mesh* m, const double* a, double c, const double* f_face,
                                  const double* uD_face, const double* gN_face, double* values, double* rhs,
-                                 void* stream) {
+                                 double* factor, void* stream) {
   if (!m || !finite_pos(c)) return PH_ERR_ARG;
   if (m->nE > 0 && (!a || !f_face)) return PH_ERR_ARG;
   if ((m->nnz > 0 && !values) || (m->L > 0 && !rhs)) return PH_ERR_ARG;
@@ -250,14 +302,22 @@ extern "C" ph_status ph_assemble(const ph_mesh* m, const double* a, double c, co
   if (m->nE == 0) return PH_OK;
   const double c20 = c / 20.0, six_over_c = 6.0 / c;
   const unsigned grid = grid_for(m->nE, 128);
-#define PH_ASM(UDV, GNV)                                                                                         \
-  k_assemble<UDV, GNV><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->tpos, m->trel, m->face_area, a, \
-                                            c20, six_over_c, f_face, uD_face, gN_face, values, rhs, m->status)
+#define PH_ASM(UDV, GNV, FACV)                                                                                 \
+  k_assemble<UDV, GNV, FACV><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->tpos, m->trel,        \
+                                                  m->face_area, a, c20, six_over_c, f_face, uD_face, gN_face, \
+                                                  values, rhs, factor, m->status)
   const bool ud = uD_face != nullptr && m->nFd > 0, gn = gN_face != nullptr && m->nFn > 0;
-  if (ud && gn) PH_ASM(true, true);
-  else if (ud) PH_ASM(true, false);
-  else if (gn) PH_ASM(false, true);
-  else PH_ASM(false, false);
+  if (factor) {
+    if (ud && gn) PH_ASM(true, true, true);
+    else if (ud) PH_ASM(true, false, true);
+    else if (gn) PH_ASM(false, true, true);
+    else PH_ASM(false, false, true);
+  } else {
+    if (ud && gn) PH_ASM(true, true, false);
+    else if (ud) PH_ASM(true, false, false);
+    else if (gn) PH_ASM(false, true, false);
+    else PH_ASM(false, false, false);
+  }
 #undef PH_ASM
   return cuda_status(launched(), "k_assemble");
 }
@@ -277,4 +337,21 @@ extern "C" ph_status ph_recover(const ph_mesh* m, const double* a, double c, con
     k_recover<false><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->face_area, a, c20, six_over_c,
                                           f_face, gN_face, lambda, u, m->status);
   return cuda_status(launched(), "k_recover");
+}
+
+extern "C" ph_status ph_recover_factored(const ph_mesh* m, const double* factor, double c, const double* f_face,
+                                         const double* gN_face, const double* lambda, double* u, void* stream) {
+  if (!m || !finite_pos(c)) return PH_ERR_ARG;
+  if (m->nE > 0 && (!factor || !f_face || !u || (m->L > 0 && !lambda))) return PH_ERR_ARG;
+  if (m->nE == 0) return PH_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double six_over_c = 6.0 / c;
+  const unsigned grid = grid_for(m->nE, 128);
+  if (gN_face != nullptr && m->nFn > 0)
+    k_recover_factored<true><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->face_area, factor,
+                                                  six_over_c, f_face, gN_face, lambda, u);
+  else
+    k_recover_factored<false><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->face_area, factor,
+                                                   six_over_c, f_face, gN_face, lambda, u);
+  return cuda_status(launched(), "k_recover_factored");
 }

@@ -4,10 +4,13 @@
 //
 // Connectivity.  The paper builds faces from edge-to-tet sparse maps
 // (Listings EdgeNum2Tetra, FacesUp).  Here every local face becomes a key
-// (v0 < v1 < v2) that is bucketed by its smallest vertex v0 (a counting sort:
-// histogram, scan, scatter), and duplicates are matched inside each bucket.
-// The result is the paper's numbering: a face's id is the rank of its first
-// occurrence in (tet, local face) order and the tet of that occurrence is T+.
+// (v0 < v1 < v2) that is counting-sorted into buckets by its largest vertex v2
+// (histogram, scan, scatter; mesh order keeps the scatter local; on refined
+// meshes the largest vertex spreads keys more evenly than the smallest), and
+// the keys of a bucket are matched against each other.  The result is the
+// paper's numbering: a face's id is the rank of its first occurrence in
+// (tet, local face) order and the tet of that occurrence is T+; it does not
+// depend on the order of entries inside a bucket.
 #include <math.h>
 
 #include "ph_internal.cuh"
@@ -49,7 +52,7 @@ __device__ __forceinline__ int3 neumann_tri(const int32_t* nb, int64_t i) {
   return make_int3(nb[3 * i], nb[3 * i + 1], nb[3 * i + 2]);
 }
 
-// 1. histogram of face keys by smallest vertex
+// 1. histogram of face keys by largest vertex
 __global__ void k_face_count(const int4* __restrict__ tet, int64_t nE, int64_t nC, const int32_t* __restrict__ nb,
                              int64_t nN, int32_t* __restrict__ cnt, unsigned* status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -57,11 +60,11 @@ __global__ void k_face_count(const int4* __restrict__ tet, int64_t nE, int64_t n
     int4 v = tet[i];
     if (!valid_tet(v, nC)) { ph_flag(status, PH_ERR_ARG); return; }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) atomicAdd(&cnt[sort3(local_face(v, k)).x], 1);
+    for (int k = 0; k < 4; ++k) atomicAdd(&cnt[sort3(local_face(v, k)).z], 1);
   } else if (i < nE + nN) {
     int3 f = neumann_tri(nb, i - nE);
     if (!valid_tri(f, nC)) { ph_flag(status, PH_ERR_ARG); return; }
-    atomicAdd(&cnt[sort3(f).x], 1);
+    atomicAdd(&cnt[sort3(f).z], 1);
   }
 }
 
@@ -77,41 +80,59 @@ __global__ void k_face_fill(const int4* __restrict__ tet, int64_t nE, int64_t nC
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       int3 s = sort3(local_face(v, k));
-      int pos = start[s.x] + atomicSub(&cnt[s.x], 1) - 1;
+      int pos = start[s.z] + atomicSub(&cnt[s.z], 1) - 1;
       entries[pos] = make_int4(s.x, s.y, s.z, (int)(4 * i + k));
     }
   } else if (i < nE + nN) {
     int3 f = neumann_tri(nb, i - nE);
     if (!valid_tri(f, nC)) return;
     int3 s = sort3(f);
-    int pos = start[s.x] + atomicSub(&cnt[s.x], 1) - 1;
+    int pos = start[s.z] + atomicSub(&cnt[s.z], 1) - 1;
     entries[pos] = make_int4(s.x, s.y, s.z, (int)i + 3 * (int)nE);  // = 4nE + (i - nE)
   }
 }
 
-// 3. match equal keys inside a bucket.  mate[slot] of a tet slot: the other
-//    tet slot of the face, -1 (Dirichlet boundary) or -2 (Neumann boundary).
+// 3. match equal keys inside a bucket (all keys of a bucket share v2).
+//    mate[slot] of a tet slot: the other tet slot of the face, -1 (Dirichlet
+//    boundary, the initial value) or -2 (Neumann boundary).  A tet entry
+//    compares itself with the LATER entries of its bucket only and writes both
+//    mates of a pair, so each pair is found once; a second match marks a face
+//    in three tets (or a Neumann triple on an interior face).  Neumann entries
+//    (boundary only, few) scan the whole bucket and must match exactly one tet
+//    entry.
 __global__ void k_face_match(const int4* __restrict__ entries, int64_t nent, const int32_t* __restrict__ start,
                              int64_t nE, int32_t* __restrict__ mate, unsigned* status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nent) return;
-  int4 e = entries[i];
-  int lo = start[e.x], hi = start[e.x + 1];
-  int nt = 0, nn = 0, tm = -1;
+  const int4 e = entries[i];
+  const int lo = start[e.z], hi = start[e.z + 1];
   const int64_t ntet = 4 * nE;
-  for (int j = lo; j < hi; ++j) {
-    if (j == i) continue;
-    int4 f = entries[j];
-    if (f.y == e.y && f.z == e.z) {
-      if (f.w < ntet) { ++nt; tm = f.w; } else { ++nn; }
-    }
-  }
   if (e.w < ntet) {
-    if (nt >= 2) ph_flag(status, PH_ERR_NONMANIFOLD);
-    if (nn >= 2 || (nt >= 1 && nn >= 1)) ph_flag(status, PH_ERR_ARG);
-    mate[e.w] = nt >= 1 ? tm : (nn >= 1 ? -2 : -1);
+    int nt = 0, nn = 0, tm = -1;
+    for (int j = (int)i + 1; j < hi; ++j) {
+      const int4 f = entries[j];
+      if (f.x == e.x && f.y == e.y) {
+        if (f.w < ntet) { ++nt; tm = f.w; } else { ++nn; }
+      }
+    }
+    if (nt + nn >= 2) ph_flag(status, nn > 0 ? PH_ERR_ARG : PH_ERR_NONMANIFOLD);
+    if (nt == 1) {
+      mate[e.w] = tm;
+      mate[tm] = e.w;
+    } else if (nn == 1) {
+      mate[e.w] = -2;
+    }
   } else {
+    int nt = 0, nn = 0, tm = -1;
+    for (int j = lo; j < hi; ++j) {
+      if (j == i) continue;
+      const int4 f = entries[j];
+      if (f.x == e.x && f.y == e.y) {
+        if (f.w < ntet) { ++nt; tm = f.w; } else { ++nn; }
+      }
+    }
     if (nt != 1 || nn != 0) ph_flag(status, PH_ERR_ARG);
+    else mate[tm] = -2;
   }
 }
 
@@ -134,15 +155,45 @@ __device__ __forceinline__ int first_rank(int4 m, int s0, int k) {
   return r;
 }
 
-// 5. face ids, T+/T-, T+'s tuple and the face kind
-__global__ void k_face_emit(const int4* __restrict__ tet, int64_t nE, const int4* __restrict__ mate4,
-                            const int32_t* __restrict__ fbase, int4* __restrict__ tface, int2* __restrict__ face_tet,
-                            int32_t* __restrict__ face_vtx, int8_t* __restrict__ face_kind) {
+// 5. per tet: face ids, T+/T-, T+'s tuple, kind and non-Neumann flag of the
+//    faces it owns (first occurrences), and the element geometry:
+//    E = rows P_i - P_0 (i = 1..3), G_e = E E', GT = G_e T0^-1 =
+//    G_e - (G_e 1) 1'/4 (T0 = I + 1 1'), |det E|, 1/|det E|.
+__global__ void k_face_emit(const double* __restrict__ coord, const int4* __restrict__ tet, int64_t nE,
+                            const int4* __restrict__ mate4, const int32_t* __restrict__ fbase,
+                            int4* __restrict__ tface, int2* __restrict__ face_tet, int32_t* __restrict__ face_vtx,
+                            int8_t* __restrict__ face_kind, int32_t* __restrict__ flag, double* __restrict__ geo,
+                            unsigned* status) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nE) return;
   int4 v = tet[t];
   int4 m = mate4[t];
   int s0 = (int)(4 * t);
+  const double* p0 = coord + 3 * (int64_t)v.x;
+  const double* p1 = coord + 3 * (int64_t)v.y;
+  const double* p2 = coord + 3 * (int64_t)v.z;
+  const double* p3 = coord + 3 * (int64_t)v.w;
+  const double e1x = p1[0] - p0[0], e1y = p1[1] - p0[1], e1z = p1[2] - p0[2];
+  const double e2x = p2[0] - p0[0], e2y = p2[1] - p0[1], e2z = p2[2] - p0[2];
+  const double e3x = p3[0] - p0[0], e3y = p3[1] - p0[1], e3z = p3[2] - p0[2];
+  const double n1x = e2y * e3z - e2z * e3y, n1y = e2z * e3x - e2x * e3z, n1z = e2x * e3y - e2y * e3x;
+  const double det = e1x * n1x + e1y * n1y + e1z * n1z;
+  const double adet = fabs(det);
+  if (!(adet > 0.0) || !(adet < INFINITY)) ph_flag(status, PH_ERR_DEGENERATE);
+  const double g00 = e1x * e1x + e1y * e1y + e1z * e1z, g01 = e1x * e2x + e1y * e2y + e1z * e2z;
+  const double g02 = e1x * e3x + e1y * e3y + e1z * e3z, g11 = e2x * e2x + e2y * e2y + e2z * e2z;
+  const double g12 = e2x * e3x + e2y * e3y + e2z * e3z, g22 = e3x * e3x + e3y * e3y + e3z * e3z;
+  const double r0 = 0.25 * (g00 + g01 + g02), r1 = 0.25 * (g01 + g11 + g12), r2 = 0.25 * (g02 + g12 + g22);
+  double2* gg = reinterpret_cast<double2*>(geo + PH_GEO_STRIDE * t);
+  gg[0] = make_double2(g00, g01);
+  gg[1] = make_double2(g02, g11);
+  gg[2] = make_double2(g12, g22);
+  gg[3] = make_double2(g00 - r0, g01 - r0);
+  gg[4] = make_double2(g02 - r0, g01 - r1);
+  gg[5] = make_double2(g11 - r1, g12 - r1);
+  gg[6] = make_double2(g02 - r2, g12 - r2);
+  gg[7] = make_double2(g22 - r2, adet);
+  gg[8] = make_double2(1.0 / adet, 0.0);
   int out[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -155,7 +206,9 @@ __global__ void k_face_emit(const int4* __restrict__ tet, int64_t nE, const int4
       face_vtx[3 * (int64_t)F] = lf.x;
       face_vtx[3 * (int64_t)F + 1] = lf.y;
       face_vtx[3 * (int64_t)F + 2] = lf.z;
-      face_kind[F] = (int8_t)(mk >= 0 ? 0 : (mk == -1 ? 1 : 2));
+      const int kind = mk >= 0 ? 0 : (mk == -1 ? 1 : 2);
+      face_kind[F] = (int8_t)kind;
+      flag[F] = kind != 2;
     } else {
       int t2 = mk >> 2, k2 = mk & 3;
       int F = fbase[t2] + first_rank(mate4[t2], 4 * t2, k2);
@@ -165,10 +218,9 @@ __global__ void k_face_emit(const int4* __restrict__ tet, int64_t nE, const int4
   tface[t] = make_int4(out[0], out[1], out[2], out[3]);
 }
 
-// 6. face areas 1/2 |(P_z - P_x) x (P_y - P_x)| and the non-Neumann flags
-__global__ void k_face_geom(const double* __restrict__ coord, const int32_t* __restrict__ face_vtx, int64_t nF,
-                            const int8_t* __restrict__ face_kind, double* __restrict__ area,
-                            int32_t* __restrict__ flag) {
+// 6. face areas 1/2 |(P_z - P_x) x (P_y - P_x)| (one thread per face)
+__global__ void k_face_area(const double* __restrict__ coord, const int32_t* __restrict__ face_vtx, int64_t nF,
+                            double* __restrict__ area) {
   int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (F >= nF) return;
   const double* x = coord + 3 * (int64_t)face_vtx[3 * F];
@@ -178,7 +230,6 @@ __global__ void k_face_geom(const double* __restrict__ coord, const int32_t* __r
   double v0 = y[0] - x[0], v1 = y[1] - x[1], v2 = y[2] - x[2];
   double cx = u1 * v2 - u2 * v1, cy = u2 * v0 - u0 * v2, cz = u0 * v1 - u1 * v0;
   area[F] = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
-  flag[F] = face_kind[F] != 2;
 }
 
 __global__ void k_mult_fix(int32_t* __restrict__ face_mult, const int8_t* __restrict__ face_kind, int64_t nF) {
@@ -277,29 +328,6 @@ __global__ void k_row_fill(const int2* __restrict__ face_tet, const int4* __rest
   }
 }
 
-// 9. element geometry: G_e = E E' (E rows P_i - P_0), |det E|, 1/|det E|
-__global__ void k_tet_geom(const double* __restrict__ coord, const int4* __restrict__ tet, int64_t nE,
-                           double* __restrict__ geo, unsigned* status) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nE) return;
-  int4 v = tet[t];
-  const double* p0 = coord + 3 * (int64_t)v.x;
-  const double* p1 = coord + 3 * (int64_t)v.y;
-  const double* p2 = coord + 3 * (int64_t)v.z;
-  const double* p3 = coord + 3 * (int64_t)v.w;
-  double e1x = p1[0] - p0[0], e1y = p1[1] - p0[1], e1z = p1[2] - p0[2];
-  double e2x = p2[0] - p0[0], e2y = p2[1] - p0[1], e2z = p2[2] - p0[2];
-  double e3x = p3[0] - p0[0], e3y = p3[1] - p0[1], e3z = p3[2] - p0[2];
-  double det = e1x * (e2y * e3z - e2z * e3y) + e1y * (e2z * e3x - e2x * e3z) + e1z * (e2x * e3y - e2y * e3x);
-  double adet = fabs(det);
-  if (!(adet > 0.0) || !(adet < INFINITY)) ph_flag(status, PH_ERR_DEGENERATE);
-  double2* g = reinterpret_cast<double2*>(geo + 8 * t);
-  g[0] = make_double2(e1x * e1x + e1y * e1y + e1z * e1z, e1x * e2x + e1y * e2y + e1z * e2z);
-  g[1] = make_double2(e1x * e3x + e1y * e3y + e1z * e3z, e2x * e2x + e2y * e2y + e2z * e2z);
-  g[2] = make_double2(e2x * e3x + e2y * e3y + e2z * e3z, e3x * e3x + e3y * e3y + e3z * e3z);
-  g[3] = make_double2(adet, 1.0 / adet);
-}
-
 __global__ void k_face_centroid(const double* __restrict__ coord, const int32_t* __restrict__ face_vtx, int64_t nF,
                                 double* __restrict__ out) {
   int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -378,7 +406,7 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   PH_CU(alloc(&entries, (size_t)nent, s), "alloc");
   PH_CU(alloc(&mate, (size_t)(4 * nE), s), "alloc");
   PH_CU(alloc(&newc, (size_t)nE + 1, s), "alloc");
-  PH_CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nC + 1), s), "memset");
+  PH_CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)nC + 1), s), "memset");
   PH_CU(cudaMemsetAsync(mate, 0xFF, sizeof(int32_t) * 4 * nE, s), "memset");
   if (nent > 0) {
     k_face_count<<<grid_for(nE + nN), kThreads, 0, s>>>(m->tet, nE, nC, neumann, nN, cnt, m->status);
@@ -412,17 +440,19 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   PH_CU(alloc(&m->face_mult, (size_t)m->nF + 1, s), "alloc");
   PH_CU(alloc(&m->face_area, (size_t)m->nF, s), "alloc");
   PH_CU(alloc(&flag, (size_t)m->nF + 1, s), "alloc");
+  PH_CU(alloc(&m->geo, (size_t)(PH_GEO_STRIDE * nE), s), "alloc");
   if (nE > 0) {
-    k_face_emit<<<grid_for(nE), kThreads, 0, s>>>(m->tet, nE, reinterpret_cast<int4*>(mate), newc, m->tface,
-                                                  m->face_tet, m->face_vtx, m->face_kind);
+    k_face_emit<<<grid_for(nE), kThreads, 0, s>>>(m->coord, m->tet, nE, reinterpret_cast<int4*>(mate), newc,
+                                                  m->tface, m->face_tet, m->face_vtx, m->face_kind, flag,
+                                                  m->geo, m->status);
     PH_CU(launched(), "k_face_emit");
+  }
+  if (m->nF > 0) {
+    k_face_area<<<grid_for(m->nF), kThreads, 0, s>>>(m->coord, m->face_vtx, m->nF, m->face_area);
+    PH_CU(launched(), "k_face_area");
   }
   free_async(mate, s); mate = nullptr;
   free_async(newc, s); newc = nullptr;
-  if (m->nF > 0) {
-    k_face_geom<<<grid_for(m->nF), kThreads, 0, s>>>(m->coord, m->face_vtx, m->nF, m->face_kind, m->face_area, flag);
-    PH_CU(launched(), "k_face_geom");
-  }
   PH_CU(cudaMemsetAsync(flag + m->nF, 0, sizeof(int32_t), s), "memset");
   PH_TRY(exclusive_scan(flag, m->face_mult, m->nF + 1, d_total, s));
   if (m->nF > 0) {
@@ -447,11 +477,6 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   }
   PH_TRY(exclusive_scan(rowlen, m->rowptr, m->L + 1, d_total, s));
   free_async(rowlen, s); rowlen = nullptr;
-  PH_CU(alloc(&m->geo, (size_t)(8 * nE), s), "alloc");
-  if (nE > 0) {
-    k_tet_geom<<<grid_for(nE), kThreads, 0, s>>>(m->coord, m->tet, nE, m->geo, m->status);
-    PH_CU(launched(), "k_tet_geom");
-  }
   PH_TRY(read_counters(d_total, m->status, s, &total, &bits));
   if (bits) { st = status_from_bits(bits); goto fail; }
   if (total >= ((int64_t)1 << 31) - 1) { st = PH_ERR_OVERFLOW; goto fail; }

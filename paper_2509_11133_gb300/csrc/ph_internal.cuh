@@ -13,6 +13,9 @@
 #define PH_NO_MULT 0x7FFFFFFF
 #define PH_BND_BIT 0x80000000u
 #define PH_ID_MASK 0x7FFFFFFF
+// Per-element geometry record (doubles): G_e = E E' (00 01 02 11 12 22),
+// GT = G_e T0^-1 row-major (9), |det E|, 1/|det E|, padding.
+#define PH_GEO_STRIDE 18
 
 struct ph_mesh {
   int device;
@@ -23,7 +26,7 @@ struct ph_mesh {
   int4* tmult;         // nE: see PH_NO_MULT / PH_BND_BIT
   int4* tpos;          // nE: CSR position of the diagonal entry of row l(F_k)
   ushort4* trel;       // nE: 3 packed 4-bit offsets (m != k, ascending m) from tpos
-  double* geo;         // nE*8: G_e (00,01,02,11,12,22), |det|, 1/|det|
+  double* geo;         // nE*PH_GEO_STRIDE: G_e, G_e T0^-1, |det|, 1/|det|
   int2* face_tet;      // nF
   int32_t* face_vtx;   // nF*3
   int8_t* face_kind;   // nF

@@ -49,4 +49,4 @@ def test_host_side_queries_without_gpu(lib):
     out = ctypes.c_void_p()
     assert lib.ph_mesh_create(None, 0, None, -1, None, 0, None, ctypes.byref(out)) == 1
     lib.ph_assemble.restype = ctypes.c_int
-    assert lib.ph_assemble(None, None, ctypes.c_double(1.0), None, None, None, None, None, None) == 1
+    assert lib.ph_assemble(None, None, ctypes.c_double(1.0), None, None, None, None, None, None, None) == 1

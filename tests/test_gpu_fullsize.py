@@ -44,12 +44,14 @@ def run_full(ph, p):
     f = np.asarray(p.f(fc["face_centroid"]), np.float64)
     rowptr, colind = mesh.csr_pattern()
     a_d, f_d = torch.as_tensor(p.a, device=dev), torch.as_tensor(f, device=dev)
-    values, rhs = mesh.assemble(a_d, p.c, f_d)
+    values, rhs, factor = mesh.assemble(a_d, p.c, f_d, factor=True)
     lam = np.random.default_rng(3).standard_normal(mesh.L)
-    u = mesh.recover(a_d, p.c, f_d, torch.as_tensor(lam, device=dev))
+    lam_d = torch.as_tensor(lam, device=dev)
+    u = mesh.recover(a_d, p.c, f_d, lam_d)
+    uf = mesh.recover_factored(factor, p.c, f_d, lam_d)
     mesh.check()
     out = dict(info=dict(mesh.info), fc=fc, f=f, lam=lam, rowptr=_host(rowptr), colind=_host(colind),
-               values=_host(values), rhs=_host(rhs), U=_host(u))
+               values=_host(values), rhs=_host(rhs), U=_host(u), U_factored=_host(uf))
     mesh.close()
     return out
 
@@ -107,6 +109,7 @@ def check_sampled_recovery(p, g, rng):
         P, f4, sig, Fk = element_inputs(p, g, t)
         U = oracle.tet_recover(P, p.a[t], p.c, f4, sig, g["lam"][fm[Fk]])
         assert np.all(np.abs(g["U"][t] - U) <= 1e-12 * np.abs(U).max())
+        assert np.all(np.abs(g["U_factored"][t] - U) <= 1e-12 * np.abs(U).max())
 
 
 def check_properties(p, g, m, k):

@@ -58,7 +58,7 @@ def run_gpu(ph, p, a=None, lam=None, solve=False):
     a_d, f_d = cu(a, torch.float64), cu(f, torch.float64)
     uD_d = None if uD is None else cu(uD, torch.float64)
     gN_d = None if gN is None else cu(gN, torch.float64)
-    values, rhs = mesh.assemble(a_d, p.c, f_d, uD_d, gN_d)
+    values, rhs, factor = mesh.assemble(a_d, p.c, f_d, uD_d, gN_d, factor=True)
     out = dict(mesh=mesh, fc=fc, f=f, uD=uD, gN=gN, rowptr=host(rowptr), colind=host(colind), values=host(values),
                rhs=host(rhs))
     if solve:
@@ -66,8 +66,10 @@ def run_gpu(ph, p, a=None, lam=None, solve=False):
         out.update(lam=host(x), iters=it, relres=rr)
         lam = out["lam"]
     if lam is not None:
-        u = mesh.recover(a_d, p.c, f_d, cu(lam, torch.float64), gN_d)
+        lam_d = cu(lam, torch.float64)
+        u = mesh.recover(a_d, p.c, f_d, lam_d, gN_d)
         out["U"] = host(u)
+        out["U_factored"] = host(mesh.recover_factored(factor, p.c, f_d, lam_d, gN_d))
     mesh.check()
     return out
 
@@ -167,6 +169,7 @@ def test_recovery_parity_given_lambda(ph, name):
     Uo = oracle.recover(p.coord, p.tet, fc, fm, p.a, p.c, g["f"], lam, g["gN"])
     scale = np.abs(Uo).max(axis=1, keepdims=True)
     assert np.all(np.abs(g["U"] - Uo) <= 1e-12 * scale)
+    assert np.all(np.abs(g["U_factored"] - Uo) <= 1e-12 * scale)
     g["mesh"].close()
 
 
@@ -178,6 +181,7 @@ def test_solve_and_recover_parity(ph, name):
     assert g["relres"] <= 1e-13
     assert np.linalg.norm(g["lam"] - o["lam"]) <= SOLVE_RTOL * np.linalg.norm(o["lam"])
     assert np.linalg.norm(g["U"] - o["U"]) <= SOLVE_RTOL * np.linalg.norm(o["U"])
+    assert np.linalg.norm(g["U_factored"] - o["U"]) <= SOLVE_RTOL * np.linalg.norm(o["U"])
     g["mesh"].close()
 
 
