@@ -86,7 +86,10 @@ typedef struct {
  * Section 2.2; it is computed on the device by bucketing face keys by their
  * smallest vertex and matching within buckets, and is bit-identical to the
  * definition (first occurrence numbering).
- * Synchronises `stream` (twice: to size the face and CSR arrays).
+ * Work already queued on `stream` is waited for, the build runs on two
+ * internal streams (connectivity at high priority, element geometry at low
+ * priority) and later work on `stream` is ordered after it.  The call blocks
+ * the host until the mesh is built (it must read the face and CSR sizes).
  * Errors: PH_ERR_ARG for ids out of [0, nC), repeated vertices in a tet, a
  * Neumann triple that is not a boundary face of the mesh or is listed twice;
  * PH_ERR_NONMANIFOLD; PH_ERR_DEGENERATE for det = 0; PH_ERR_OVERFLOW when

@@ -12,6 +12,9 @@
 // (tet, local face) order and the tet of that occurrence is T+; it does not
 // depend on the order of entries inside a bucket.
 #include <math.h>
+#include <string.h>
+
+#include <mutex>
 
 #include "ph_internal.cuh"
 
@@ -156,44 +159,16 @@ __device__ __forceinline__ int first_rank(int4 m, int s0, int k) {
 }
 
 // 5. per tet: face ids, T+/T-, T+'s tuple, kind and non-Neumann flag of the
-//    faces it owns (first occurrences), and the element geometry:
-//    E = rows P_i - P_0 (i = 1..3), G_e = E E', GT = G_e T0^-1 =
-//    G_e - (G_e 1) 1'/4 (T0 = I + 1 1'), |det E|, 1/|det E|.
-__global__ void k_face_emit(const double* __restrict__ coord, const int4* __restrict__ tet, int64_t nE,
-                            const int4* __restrict__ mate4, const int32_t* __restrict__ fbase,
-                            int4* __restrict__ tface, int2* __restrict__ face_tet, int32_t* __restrict__ face_vtx,
-                            int8_t* __restrict__ face_kind, int32_t* __restrict__ flag, double* __restrict__ geo,
-                            unsigned* status) {
+//    faces it owns (first occurrences).
+__global__ void k_face_emit(const int4* __restrict__ tet, int64_t nE, const int4* __restrict__ mate4,
+                            const int32_t* __restrict__ fbase, int4* __restrict__ tface, int2* __restrict__ face_tet,
+                            int32_t* __restrict__ face_vtx, int8_t* __restrict__ face_kind,
+                            int32_t* __restrict__ flag) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nE) return;
   int4 v = tet[t];
   int4 m = mate4[t];
   int s0 = (int)(4 * t);
-  const double* p0 = coord + 3 * (int64_t)v.x;
-  const double* p1 = coord + 3 * (int64_t)v.y;
-  const double* p2 = coord + 3 * (int64_t)v.z;
-  const double* p3 = coord + 3 * (int64_t)v.w;
-  const double e1x = p1[0] - p0[0], e1y = p1[1] - p0[1], e1z = p1[2] - p0[2];
-  const double e2x = p2[0] - p0[0], e2y = p2[1] - p0[1], e2z = p2[2] - p0[2];
-  const double e3x = p3[0] - p0[0], e3y = p3[1] - p0[1], e3z = p3[2] - p0[2];
-  const double n1x = e2y * e3z - e2z * e3y, n1y = e2z * e3x - e2x * e3z, n1z = e2x * e3y - e2y * e3x;
-  const double det = e1x * n1x + e1y * n1y + e1z * n1z;
-  const double adet = fabs(det);
-  if (!(adet > 0.0) || !(adet < INFINITY)) ph_flag(status, PH_ERR_DEGENERATE);
-  const double g00 = e1x * e1x + e1y * e1y + e1z * e1z, g01 = e1x * e2x + e1y * e2y + e1z * e2z;
-  const double g02 = e1x * e3x + e1y * e3y + e1z * e3z, g11 = e2x * e2x + e2y * e2y + e2z * e2z;
-  const double g12 = e2x * e3x + e2y * e3y + e2z * e3z, g22 = e3x * e3x + e3y * e3y + e3z * e3z;
-  const double r0 = 0.25 * (g00 + g01 + g02), r1 = 0.25 * (g01 + g11 + g12), r2 = 0.25 * (g02 + g12 + g22);
-  double2* gg = reinterpret_cast<double2*>(geo + PH_GEO_STRIDE * t);
-  gg[0] = make_double2(g00, g01);
-  gg[1] = make_double2(g02, g11);
-  gg[2] = make_double2(g12, g22);
-  gg[3] = make_double2(g00 - r0, g01 - r0);
-  gg[4] = make_double2(g02 - r0, g01 - r1);
-  gg[5] = make_double2(g11 - r1, g12 - r1);
-  gg[6] = make_double2(g02 - r2, g12 - r2);
-  gg[7] = make_double2(g22 - r2, adet);
-  gg[8] = make_double2(1.0 / adet, 0.0);
   int out[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -216,6 +191,40 @@ __global__ void k_face_emit(const double* __restrict__ coord, const int4* __rest
     }
   }
   tface[t] = make_int4(out[0], out[1], out[2], out[3]);
+}
+
+// Element geometry (needs only the inputs, so it runs beside connectivity):
+// E = rows P_i - P_0 (i = 1..3), G_e = E E', GT = G_e T0^-1 = G_e - (G_e 1) 1'/4
+// (T0 = I + 1 1'), |det E|, 1/|det E|.
+__global__ void k_tet_geom(const double* __restrict__ coord, const int4* __restrict__ tet, int64_t nE,
+                           double* __restrict__ geo, unsigned* status) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nE) return;
+  const int4 v = tet[t];
+  const double* p0 = coord + 3 * (int64_t)v.x;
+  const double* p1 = coord + 3 * (int64_t)v.y;
+  const double* p2 = coord + 3 * (int64_t)v.z;
+  const double* p3 = coord + 3 * (int64_t)v.w;
+  const double e1x = p1[0] - p0[0], e1y = p1[1] - p0[1], e1z = p1[2] - p0[2];
+  const double e2x = p2[0] - p0[0], e2y = p2[1] - p0[1], e2z = p2[2] - p0[2];
+  const double e3x = p3[0] - p0[0], e3y = p3[1] - p0[1], e3z = p3[2] - p0[2];
+  const double det = e1x * (e2y * e3z - e2z * e3y) + e1y * (e2z * e3x - e2x * e3z) + e1z * (e2x * e3y - e2y * e3x);
+  const double adet = fabs(det);
+  if (!(adet > 0.0) || !(adet < INFINITY)) ph_flag(status, PH_ERR_DEGENERATE);
+  const double g00 = e1x * e1x + e1y * e1y + e1z * e1z, g01 = e1x * e2x + e1y * e2y + e1z * e2z;
+  const double g02 = e1x * e3x + e1y * e3y + e1z * e3z, g11 = e2x * e2x + e2y * e2y + e2z * e2z;
+  const double g12 = e2x * e3x + e2y * e3y + e2z * e3z, g22 = e3x * e3x + e3y * e3y + e3z * e3z;
+  const double r0 = 0.25 * (g00 + g01 + g02), r1 = 0.25 * (g01 + g11 + g12), r2 = 0.25 * (g02 + g12 + g22);
+  double2* gg = reinterpret_cast<double2*>(geo + PH_GEO_STRIDE * t);
+  gg[0] = make_double2(g00, g01);
+  gg[1] = make_double2(g02, g11);
+  gg[2] = make_double2(g12, g22);
+  gg[3] = make_double2(g00 - r0, g01 - r0);
+  gg[4] = make_double2(g02 - r0, g01 - r1);
+  gg[5] = make_double2(g11 - r1, g12 - r1);
+  gg[6] = make_double2(g02 - r2, g12 - r2);
+  gg[7] = make_double2(g22 - r2, adet);
+  gg[8] = make_double2(1.0 / adet, 0.0);
 }
 
 // 6. face areas 1/2 |(P_z - P_x) x (P_y - P_x)| (one thread per face)
@@ -357,13 +366,38 @@ static void mesh_free(ph_mesh* m, cudaStream_t s) {
   delete m;
 }
 
-// Synchronise and read a device int64 total and the status word.
-static ph_status read_counters(int64_t* d_total, unsigned* d_status, cudaStream_t s, int64_t* total,
+// Synchronise and read n device int64 counters and the status word.
+static ph_status read_counters(const int64_t* d_tot, int n, unsigned* d_status, cudaStream_t s, int64_t* tot,
                                unsigned* status) {
-  cudaError_t e = cudaMemcpyAsync(total, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaMemcpyAsync(tot, d_tot, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(status, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return cuda_status(e, "mesh_create sync");
+}
+
+// Two internal streams per device for ph_mesh_create: connectivity (integer
+// and memory work) runs on a high-priority stream and element geometry (FP64
+// work) on a low-priority one, so geometry blocks fill the SM slots the
+// connectivity kernels leave free.  Both are forked from and joined back into
+// the caller's stream.
+static std::mutex g_aux_mu;
+static cudaStream_t g_hi[64], g_lo[64];
+
+static cudaError_t aux_streams(int dev, cudaStream_t* hi, cudaStream_t* lo) {
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_aux_mu);
+  if (!g_hi[dev]) {
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamCreateWithPriority(&g_hi[dev], cudaStreamNonBlocking, greatest);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamCreateWithPriority(&g_lo[dev], cudaStreamNonBlocking, least);
+    if (e != cudaSuccess) return e;
+  }
+  *hi = g_hi[dev];
+  *lo = g_lo[dev];
+  return cudaSuccess;
 }
 
 #define PH_TRY(expr)                    \
@@ -379,26 +413,47 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   *out = nullptr;
   if (nE < 0 || nC < 0 || nN < 0 || (nE > 0 && (!coord || !tet)) || (nN > 0 && !neumann)) return PH_ERR_ARG;
   if (4 * nE + nN >= ((int64_t)1 << 31) - 1 || nC >= ((int64_t)1 << 31) - 1) return PH_ERR_OVERFLOW;
-  cudaStream_t s = (cudaStream_t)stream;
+  cudaStream_t us = (cudaStream_t)stream;  // caller's stream: fork and join only
+  cudaStream_t s = nullptr, g = nullptr;    // connectivity (high priority), geometry (low)
+  cudaEvent_t ev_in = nullptr, ev_emit = nullptr, ev_geo = nullptr, ev_done = nullptr;
+  bool forked = false;
   ph_status st = PH_OK;
   ph_mesh* m = new ph_mesh();
   memset(m, 0, sizeof *m);
   int32_t *cnt = nullptr, *start = nullptr, *mate = nullptr, *newc = nullptr, *flag = nullptr, *rowlen = nullptr;
   int4* entries = nullptr;
-  int64_t* d_total = nullptr;
-  int64_t total = 0;
+  int64_t* d_tot = nullptr;  // [0] scan total, [1] L, [2] nnz
+  int64_t tot[3] = {0, 0, 0};
   unsigned bits = 0;
   const int64_t nent = 4 * nE + nN;
   PH_CU(cudaGetDevice(&m->device), "cudaGetDevice");
+  PH_CU(aux_streams(m->device, &s, &g), "internal streams");
+  PH_CU(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming), "event");
+  PH_CU(cudaEventCreateWithFlags(&ev_emit, cudaEventDisableTiming), "event");
+  PH_CU(cudaEventCreateWithFlags(&ev_geo, cudaEventDisableTiming), "event");
+  PH_CU(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming), "event");
+  // the inputs are ordered on the caller's stream
+  PH_CU(cudaEventRecord(ev_in, us), "event");
+  PH_CU(cudaStreamWaitEvent(s, ev_in, 0), "event");
+  forked = true;
   m->nE = nE;
   m->nC = nC;
   PH_CU(alloc(&m->status, 1, s), "alloc");
   PH_CU(cudaMemsetAsync(m->status, 0, sizeof(unsigned), s), "memset");
-  PH_CU(alloc(&d_total, 1, s), "alloc");
+  PH_CU(alloc(&d_tot, 3, s), "alloc");
   PH_CU(alloc(&m->coord, (size_t)(3 * nC), s), "alloc coord");
   PH_CU(alloc(&m->tet, (size_t)nE, s), "alloc tet");
+  PH_CU(alloc(&m->geo, (size_t)(PH_GEO_STRIDE * nE), s), "alloc");
   if (nC > 0) PH_CU(cudaMemcpyAsync(m->coord, coord, sizeof(double) * 3 * nC, cudaMemcpyDeviceToDevice, s), "copy");
   if (nE > 0) PH_CU(cudaMemcpyAsync(m->tet, tet, sizeof(int4) * nE, cudaMemcpyDeviceToDevice, s), "copy");
+
+  // --- element geometry on the low-priority stream ---------------------------
+  PH_CU(cudaEventRecord(ev_in, s), "event");
+  PH_CU(cudaStreamWaitEvent(g, ev_in, 0), "event");
+  if (nE > 0) {
+    k_tet_geom<<<grid_for(nE), kThreads, 0, g>>>(m->coord, m->tet, nE, m->geo, m->status);
+    PH_CU(launched(), "k_tet_geom");
+  }
 
   // --- connectivity -------------------------------------------------------
   PH_CU(alloc(&cnt, (size_t)nC + 1, s), "alloc");
@@ -412,7 +467,7 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
     k_face_count<<<grid_for(nE + nN), kThreads, 0, s>>>(m->tet, nE, nC, neumann, nN, cnt, m->status);
     PH_CU(launched(), "k_face_count");
   }
-  PH_TRY(exclusive_scan(cnt, start, nC + 1, d_total, s));
+  PH_TRY(exclusive_scan(cnt, start, nC + 1, d_tot, s));
   if (nent > 0) {
     k_face_fill<<<grid_for(nE + nN), kThreads, 0, s>>>(m->tet, nE, nC, neumann, nN, start, cnt, entries);
     PH_CU(launched(), "k_face_fill");
@@ -424,11 +479,11 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
     PH_CU(launched(), "k_new_count");
   }
   PH_CU(cudaMemsetAsync(newc + nE, 0, sizeof(int32_t), s), "memset");
-  PH_TRY(exclusive_scan(newc, newc, nE + 1, d_total, s));
-  PH_TRY(read_counters(d_total, m->status, s, &total, &bits));
+  PH_TRY(exclusive_scan(newc, newc, nE + 1, d_tot, s));
+  PH_TRY(read_counters(d_tot, 1, m->status, s, tot, &bits));
   if (bits) { st = status_from_bits(bits); goto fail; }
-  if (total >= ((int64_t)1 << 31) - 1) { st = PH_ERR_OVERFLOW; goto fail; }
-  m->nF = total;
+  if (tot[0] >= ((int64_t)1 << 31) - 1) { st = PH_ERR_OVERFLOW; goto fail; }
+  m->nF = tot[0];
   free_async(cnt, s); cnt = nullptr;
   free_async(start, s); start = nullptr;
   free_async(entries, s); entries = nullptr;
@@ -440,47 +495,46 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   PH_CU(alloc(&m->face_mult, (size_t)m->nF + 1, s), "alloc");
   PH_CU(alloc(&m->face_area, (size_t)m->nF, s), "alloc");
   PH_CU(alloc(&flag, (size_t)m->nF + 1, s), "alloc");
-  PH_CU(alloc(&m->geo, (size_t)(PH_GEO_STRIDE * nE), s), "alloc");
   if (nE > 0) {
-    k_face_emit<<<grid_for(nE), kThreads, 0, s>>>(m->coord, m->tet, nE, reinterpret_cast<int4*>(mate), newc,
-                                                  m->tface, m->face_tet, m->face_vtx, m->face_kind, flag,
-                                                  m->geo, m->status);
+    k_face_emit<<<grid_for(nE), kThreads, 0, s>>>(m->tet, nE, reinterpret_cast<int4*>(mate), newc, m->tface,
+                                                  m->face_tet, m->face_vtx, m->face_kind, flag);
     PH_CU(launched(), "k_face_emit");
-  }
-  if (m->nF > 0) {
-    k_face_area<<<grid_for(m->nF), kThreads, 0, s>>>(m->coord, m->face_vtx, m->nF, m->face_area);
-    PH_CU(launched(), "k_face_area");
   }
   free_async(mate, s); mate = nullptr;
   free_async(newc, s); newc = nullptr;
+  // face areas on the second stream (after the face tuples exist)
+  PH_CU(cudaEventRecord(ev_emit, s), "event");
+  PH_CU(cudaStreamWaitEvent(g, ev_emit, 0), "event");
+  if (m->nF > 0) {
+    k_face_area<<<grid_for(m->nF), kThreads, 0, g>>>(m->coord, m->face_vtx, m->nF, m->face_area);
+    PH_CU(launched(), "k_face_area");
+  }
+
+  // --- multipliers and CSR pattern ----------------------------------------
   PH_CU(cudaMemsetAsync(flag + m->nF, 0, sizeof(int32_t), s), "memset");
-  PH_TRY(exclusive_scan(flag, m->face_mult, m->nF + 1, d_total, s));
+  PH_TRY(exclusive_scan(flag, m->face_mult, m->nF + 1, d_tot + 1, s));  // L -> d_tot[1]
   if (m->nF > 0) {
     k_mult_fix<<<grid_for(m->nF), kThreads, 0, s>>>(m->face_mult, m->face_kind, m->nF);
     PH_CU(launched(), "k_mult_fix");
   }
   free_async(flag, s); flag = nullptr;
-  // L = number of non-Neumann faces; read it together with the row lengths below
-  {
-    int64_t L = 0;
-    PH_TRY(read_counters(d_total, m->status, s, &L, &bits));
-    if (bits) { st = status_from_bits(bits); goto fail; }
-    m->L = L;
-  }
+  // rows are indexed by multiplier id < L <= nF: size the row arrays by nF
+  // (rows L..nF-1 stay empty) and learn L with nnz at the next synchronisation
   PH_CU(alloc(&m->tmult, (size_t)nE, s), "alloc");
-  PH_CU(alloc(&rowlen, (size_t)m->L + 1, s), "alloc");
-  PH_CU(alloc(&m->rowptr, (size_t)m->L + 1, s), "alloc");
-  PH_CU(cudaMemsetAsync(rowlen, 0, sizeof(int32_t) * (m->L + 1), s), "memset");
+  PH_CU(alloc(&rowlen, (size_t)m->nF + 1, s), "alloc");
+  PH_CU(alloc(&m->rowptr, (size_t)m->nF + 1, s), "alloc");
+  PH_CU(cudaMemsetAsync(rowlen, 0, sizeof(int32_t) * (m->nF + 1), s), "memset");
   if (nE > 0) {
     k_tet_mult<<<grid_for(nE), kThreads, 0, s>>>(m->tface, nE, m->face_mult, m->face_tet, m->tmult, rowlen);
     PH_CU(launched(), "k_tet_mult");
   }
-  PH_TRY(exclusive_scan(rowlen, m->rowptr, m->L + 1, d_total, s));
+  PH_TRY(exclusive_scan(rowlen, m->rowptr, m->nF + 1, d_tot + 2, s));  // nnz -> d_tot[2]
   free_async(rowlen, s); rowlen = nullptr;
-  PH_TRY(read_counters(d_total, m->status, s, &total, &bits));
+  PH_TRY(read_counters(d_tot, 3, m->status, s, tot, &bits));
   if (bits) { st = status_from_bits(bits); goto fail; }
-  if (total >= ((int64_t)1 << 31) - 1) { st = PH_ERR_OVERFLOW; goto fail; }
-  m->nnz = total;
+  if (tot[2] >= ((int64_t)1 << 31) - 1) { st = PH_ERR_OVERFLOW; goto fail; }
+  m->L = tot[1];
+  m->nnz = tot[2];
 
   // --- CSR columns and scatter positions ----------------------------------
   PH_CU(alloc(&m->colind, (size_t)m->nnz, s), "alloc");
@@ -495,22 +549,38 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
                                                     reinterpret_cast<unsigned short*>(m->trel), m->status);
     PH_CU(launched(), "k_row_fill");
   }
-  free_async(d_total, s); d_total = nullptr;
+  // join the geometry stream, then report any error of either stream
+  PH_CU(cudaEventRecord(ev_geo, g), "event");
+  PH_CU(cudaStreamWaitEvent(s, ev_geo, 0), "event");
+  free_async(d_tot, s); d_tot = nullptr;
   {
     unsigned b2 = 0;
     PH_CU(cudaMemcpyAsync(&b2, m->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "copy");
     PH_CU(cudaStreamSynchronize(s), "sync");
     if (b2) { st = status_from_bits(b2); goto fail; }
   }
+  // later work on the caller's stream sees the finished mesh
+  PH_CU(cudaEventRecord(ev_done, s), "event");
+  PH_CU(cudaStreamWaitEvent(us, ev_done, 0), "event");
+  forked = false;
   // face kinds: every interior face has two slots and a boundary face one,
   // so 4 nE = 2 nFi + (nF - nFi); Neumann faces are the ones without multiplier
   m->nFi = 4 * nE - m->nF;
   m->nFn = m->nF - m->L;
   m->nFd = m->nF - m->nFi - m->nFn;
+  cudaEventDestroy(ev_in);
+  cudaEventDestroy(ev_emit);
+  cudaEventDestroy(ev_geo);
+  cudaEventDestroy(ev_done);
   *out = m;
   return PH_OK;
 
 fail:
+  if (forked && g && s && ev_geo) {  // nothing is freed before the geometry stream is done
+    cudaEventRecord(ev_geo, g);
+    cudaStreamWaitEvent(s, ev_geo, 0);
+  }
+  if (!s) s = us;
   free_async(cnt, s);
   free_async(start, s);
   free_async(entries, s);
@@ -518,8 +588,16 @@ fail:
   free_async(newc, s);
   free_async(flag, s);
   free_async(rowlen, s);
-  free_async(d_total, s);
+  free_async(d_tot, s);
   mesh_free(m, s);
+  if (ev_in) cudaEventDestroy(ev_in);
+  if (ev_emit) cudaEventDestroy(ev_emit);
+  if (forked && ev_done) {  // the caller's stream waits for the frees
+    cudaEventRecord(ev_done, s);
+    cudaStreamWaitEvent(us, ev_done, 0);
+  }
+  if (ev_geo) cudaEventDestroy(ev_geo);
+  if (ev_done) cudaEventDestroy(ev_done);
   return st;
 }
 
