@@ -223,6 +223,36 @@ ph_status ph_solve_pcg_noalloc(int64_t n, const int32_t* rowptr, const int32_t* 
                                double* relres, void* stream);
 
 /*
+ * y = H x for a CSR matrix (rowptr [n+1], colind, values) and x [n], y [n]
+ * (float64 device arrays).  One kernel, no synchronisation.
+ */
+ph_status ph_spmv(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* values, const double* x,
+                  double* y, void* stream);
+
+/*
+ * Adjoint of the condensed path.  The paper has no counterpart (it computes
+ * no gradients).  For the misfit
+ *     J = 1/2 sum_T e_T' M(T) e_T,   e_T = U_T - U_obs,T
+ * (the L2 norm of a broken P1 difference; M(T) of Eq. M(T)), the gradient with
+ * respect to theta_T = log a_T follows from the adjoint of the symmetric saddle
+ * system of Eq. VectorForm:
+ *   1. ph_adjoint_rhs:  rhs_q = -sum_T P_T' C(T) A(T)^-1 M(T) e_T;
+ *   2. solve H q = rhs_q with the H of the forward assembly (ph_solve_pcg);
+ *   3. ph_adjoint_grad: grad_T = -a_T p_T' K(T) U_T with
+ *      p_T = A(T)^-1 (M(T) e_T + C(T)' q_T).
+ * u, u_obs [nE*4] (values at the element vertices, as ph_recover writes them);
+ * factor [nE*10] from ph_assemble with the same a and c; q [L]; grad [nE].
+ * ph_misfit writes J to the device scalar *J (deterministic reduction; it
+ * allocates 2.4 KB of workspace from the library's pool).
+ * Each call enqueues 1-2 kernels; no synchronisation.
+ */
+ph_status ph_misfit(const ph_mesh* mesh, const double* u, const double* u_obs, double* J, void* stream);
+ph_status ph_adjoint_rhs(const ph_mesh* mesh, const double* factor, double c, const double* u, const double* u_obs,
+                         double* rhs_q, void* stream);
+ph_status ph_adjoint_grad(const ph_mesh* mesh, const double* a, const double* factor, double c, const double* u,
+                          const double* u_obs, const double* q, double* grad, void* stream);
+
+/*
  * Synchronise `stream` and return (then clear) the mesh's device status word:
  * PH_OK or the first error a kernel recorded since the last check.
  */

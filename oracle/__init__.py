@@ -19,6 +19,9 @@ Functions and the passage each one follows:
   solve              Eq. schur, S Lambda = rhs (a library sparse/dense solve)
   recover            Algorithm 1 second loop
   element_blocks     Eq. VectorForm blocks (monolithic check)
+  misfit, monolithic, adjoint_gradient
+                     gradient of J = 1/2 sum_T e' M(T) e with respect to
+                     log a_T through Eq. VectorForm (not in the paper)
 """
 from __future__ import annotations
 
@@ -260,3 +263,84 @@ def pipeline(coord, tet, a, c, f_fn, uD_fn=None, gN_fn=None, neumann=None, do_so
         U = recover(coord, tet, fc, fm, a, c, f_face, lam, gN_face)
         out.update(lam=lam, U=U)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Adjoint (not in the paper): gradient of a misfit with respect to log a_T
+# ---------------------------------------------------------------------------
+def misfit(coord, tet, U, U_obs):
+    """J = 1/2 sum_T e_T' M(T) e_T, e = U - U_obs (the L2 norm of the broken P1
+    difference, M(T) of Eq. M(T))."""
+    J = 0.0
+    for t in range(tet.shape[0]):
+        M = tet_matrices(coord[tet[t]])["M"]
+        e = U[t] - U_obs[t]
+        J += 0.5 * e @ M @ e
+    return J
+
+
+def monolithic(coord, tet, fc, face_mult, L, a, c, f_face, uD_face=None, gN_face=None):
+    """The block saddle system of Eq. VectorForm, K [U; Lambda] = [B; -b_D]
+    with K = [[A, -C'], [-C, 0]], as a scipy sparse matrix and right side."""
+    import scipy.sparse as sp
+    nE = tet.shape[0]
+    N = 4 * nE
+    rows, cols, vals = [], [], []
+    rhs = np.zeros(N + L)
+    for t in range(nE):
+        A, C, B = element_blocks(t, coord, tet, fc, a, c, f_face, gN_face)
+        idx = 4 * t + np.arange(4)
+        rows.append(np.repeat(idx, 4)); cols.append(np.tile(idx, 4)); vals.append(A.ravel())
+        rhs[idx] = B
+        for k in range(4):
+            l = face_mult[fc["tet_face"][t, k] & 0x7FFFFFFF]
+            if l < 0:
+                continue
+            rows.append(np.full(4, N + l)); cols.append(idx); vals.append(-C[k])
+            rows.append(idx); cols.append(np.full(4, N + l)); vals.append(-C[k])
+    if uD_face is not None:
+        dir_ = np.where(fc["face_kind"] == KIND_DIRICHLET)[0]
+        fv = fc["face_vtx"][dir_]
+        x, y, z = coord[fv[:, 0]], coord[fv[:, 1]], coord[fv[:, 2]]
+        area = 0.5 * np.linalg.norm(np.cross(z - x, y - x), axis=1)
+        rhs[N + face_mult[dir_]] = -area * uD_face[dir_]
+    K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N + L, N + L))
+    return K, rhs
+
+
+def adjoint_gradient(coord, tet, a, c, f_fn, U_obs, uD_fn=None, gN_fn=None, neumann=None):
+    """dJ/d(log a_T) by the adjoint of Eq. VectorForm.
+
+    Forward: K [U; Lambda] = [B; -b_D].  J = 1/2 sum_T e_T' M(T) e_T.
+    Adjoint: K' [p; q] = [dJ/dU; 0] = [M e; 0] (K is symmetric).
+    Since only A(T) = a_T K(T) + c M(T) depends on theta_T = log a_T, with
+    dA(T)/dtheta_T = a_T K(T):   dJ/dtheta_T = -a_T p_T' K(T) U_T.
+    Solved with a sparse direct solver on the whole saddle system (small
+    meshes only).  Returns (J, grad, U, Lambda)."""
+    import scipy.sparse.linalg as spla
+    fc = faces(tet, coord.shape[0], neumann)
+    fm, L = multipliers(fc["face_kind"])
+    cen = face_centroids(coord, fc["face_vtx"])
+    f_face = np.asarray(f_fn(cen), np.float64)
+    uD_face = None if uD_fn is None else np.asarray(uD_fn(cen), np.float64)
+    gN_face = None if gN_fn is None else np.asarray(gN_fn(cen), np.float64)
+    K, rhs = monolithic(coord, tet, fc, fm, L, a, c, f_face, uD_face, gN_face)
+    K = K.tocsc()
+    lu = spla.splu(K)
+    sol = lu.solve(rhs)
+    nE = tet.shape[0]
+    U = sol[:4 * nE].reshape(nE, 4)
+    lam = sol[4 * nE:]
+    e = U - U_obs
+    J = 0.0
+    src = np.zeros(4 * nE + L)
+    Ks = []
+    for t in range(nE):
+        m = tet_matrices(coord[tet[t]])
+        J += 0.5 * e[t] @ m["M"] @ e[t]
+        src[4 * t:4 * t + 4] = m["M"] @ e[t]
+        Ks.append(m["K"])
+    adj = lu.solve(src, trans="T")
+    p = adj[:4 * nE].reshape(nE, 4)
+    grad = np.array([-a[t] * p[t] @ Ks[t] @ U[t] for t in range(nE)])
+    return J, grad, U, lam

@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "PH_OK", 1: "PH_ERR_ARG", 2: "PH_ERR_DEGENERATE", 3: "PH_ERR_
 # Every symbol declared in include/ph.h.
 EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces", "ph_csr_pattern", "ph_assemble",
            "ph_recover", "ph_solve_pcg", "ph_mesh_check", "ph_status_string", "ph_last_error_message",
-           "ph_launch_count", "ph_solve_pcg_noalloc", "ph_recover_factored")
+           "ph_launch_count", "ph_solve_pcg_noalloc", "ph_recover_factored", "ph_spmv", "ph_misfit",
+           "ph_adjoint_rhs", "ph_adjoint_grad")
 
 
 class PHError(RuntimeError):
@@ -71,6 +72,10 @@ def load(path: str | None = None):
         "ph_solve_pcg": [I64, P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P],
         "ph_solve_pcg_noalloc": [I64, P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P],
         "ph_mesh_check": [P, P],
+        "ph_spmv": [I64, P, P, P, P, P, P],
+        "ph_misfit": [P, P, P, P, P],
+        "ph_adjoint_rhs": [P, P, D, P, P, P, P],
+        "ph_adjoint_grad": [P, P, P, D, P, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -153,6 +158,14 @@ def ph_solve_pcg_noalloc(rowptr, colind, values, rhs, x=None, rtol=1e-12, maxit=
 
 
 PH_PCG_NOALLOC_MAX_N = 262144
+
+
+def ph_spmv(rowptr, colind, values, x, y=None, stream=None):
+    n = x.numel()
+    y = torch.empty_like(x) if y is None else y
+    _check(load().ph_spmv(n, _ptr(rowptr), _ptr(colind), _ptr(values), _ptr(x), _ptr(y), _stream(stream)),
+           "ph_spmv")
+    return y
 
 
 class Mesh:
@@ -269,9 +282,68 @@ class Mesh:
                                           _ptr(u), _stream(stream)), "ph_recover_factored")
         return u
 
+    def misfit(self, u, u_obs, stream=None):
+        """J = 1/2 sum_T e' M(T) e as a 0-dim CUDA tensor."""
+        _need(u, torch.float64, 4 * self.nE, "u")
+        _need(u_obs, torch.float64, 4 * self.nE, "u_obs")
+        J = torch.empty((), dtype=torch.float64, device=self.device)
+        _check(load().ph_misfit(self._h, _ptr(u), _ptr(u_obs), _ptr(J), _stream(stream)), "ph_misfit")
+        return J
+
+    def adjoint_rhs(self, factor, c, u, u_obs, rhs_q=None, stream=None):
+        _need(factor, torch.float64, 10 * self.nE, "factor")
+        rhs_q = self._empty(self.L, torch.float64) if rhs_q is None else _need(rhs_q, torch.float64, self.L, "rhs_q")
+        _check(load().ph_adjoint_rhs(self._h, _ptr(factor), float(c), _ptr(u), _ptr(u_obs), _ptr(rhs_q),
+                                     _stream(stream)), "ph_adjoint_rhs")
+        return rhs_q
+
+    def adjoint_grad(self, a, factor, c, u, u_obs, q, grad=None, stream=None):
+        _need(a, torch.float64, self.nE, "a")
+        _need(q, torch.float64, self.L, "q")
+        grad = self._empty(self.nE, torch.float64) if grad is None else _need(grad, torch.float64, self.nE, "grad")
+        _check(load().ph_adjoint_grad(self._h, _ptr(a), _ptr(factor), float(c), _ptr(u), _ptr(u_obs), _ptr(q),
+                                      _ptr(grad), _stream(stream)), "ph_adjoint_grad")
+        return grad
+
     def check(self, stream=None):
         _check(load().ph_mesh_check(self._h, _stream(stream)), "ph_mesh_check")
 
 
 def ph_mesh_create(coord, tet, neumann=None, stream=None) -> Mesh:
     return Mesh(coord, tet, neumann, stream)
+
+
+class MisfitFunction(torch.autograd.Function):
+    """J(log a) = 1/2 sum_T e_T' M(T) e_T, e = U(a) - U_obs, through assembly,
+    condensation, the PCG solve and recovery; backward is the hand-written
+    adjoint (ph_adjoint_rhs, a second solve with the same H, ph_adjoint_grad).
+
+    apply(log_a, mesh, c, f_face, u_obs, uD_face, gN_face, rtol, maxit)
+    """
+
+    @staticmethod
+    def forward(ctx, log_a, mesh, c, f_face, u_obs, uD_face=None, gN_face=None, rtol=1e-12, maxit=50000):
+        a = torch.exp(log_a)
+        rowptr, colind = mesh.csr_pattern()
+        values, rhs, factor = mesh.assemble(a, c, f_face, uD_face, gN_face, factor=True)
+        lam, _, _, _ = ph_solve_pcg(rowptr, colind, values, rhs, rtol=rtol, maxit=maxit)
+        u = mesh.recover_factored(factor, c, f_face, lam, gN_face)
+        J = mesh.misfit(u, u_obs)
+        ctx.mesh, ctx.c, ctx.rtol, ctx.maxit = mesh, c, rtol, maxit
+        ctx.csr = (rowptr, colind)
+        ctx.save_for_backward(a, values, factor, u, u_obs)
+        return J
+
+    @staticmethod
+    def backward(ctx, gJ):
+        a, values, factor, u, u_obs = ctx.saved_tensors
+        mesh = ctx.mesh
+        rhs_q = mesh.adjoint_rhs(factor, ctx.c, u, u_obs)
+        q, _, _, _ = ph_solve_pcg(*ctx.csr, values, rhs_q, rtol=ctx.rtol, maxit=ctx.maxit)
+        grad = mesh.adjoint_grad(a, factor, ctx.c, u, u_obs, q)
+        return gJ * grad, None, None, None, None, None, None, None, None
+
+
+def misfit(log_a, mesh, c, f_face, u_obs, uD_face=None, gN_face=None, rtol=1e-12, maxit=50000):
+    """Differentiable misfit (see MisfitFunction)."""
+    return MisfitFunction.apply(log_a, mesh, c, f_face, u_obs, uD_face, gN_face, rtol, maxit)

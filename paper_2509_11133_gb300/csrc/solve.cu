@@ -9,11 +9,16 @@
 namespace {
 
 constexpr int RT = 256;   // threads per block
-constexpr int RB = 304;   // blocks (2 x 152 SMs) for vector kernels and partial sums
+constexpr int RB = 1216;  // blocks (8 x 152 SMs) for vector kernels and partial sums
 
 struct Scalars {
-  double rz, pq, alpha, beta, rr, bb;
+  double rz, pq, alpha, beta, rr, bb, rz_next;
 };
+
+// Workspace of one solve (doubles): r, p, q, dinv (4 n), then the partial sums
+// part[0, RB) = p.q, part[RB, 2RB) = r.z, part[2RB, 3RB) = r.r, then Scalars
+// and a flag word.
+constexpr size_t kPart = 3 * (size_t)RB;
 
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double sm[RT / 32];
@@ -27,6 +32,13 @@ __device__ __forceinline__ double block_sum(double v) {
   }
   __syncthreads();
   return r;  // valid in thread 0
+}
+
+// Sum of part[off, off + RB) in a fixed order (every caller gets the same value).
+__device__ __forceinline__ double sum_partials(const double* __restrict__ part, int off) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < RB; i += RT) v += part[off + i];
+  return block_sum(v);
 }
 
 __global__ void __launch_bounds__(RT) k_pcg_init(int64_t n, const int32_t* __restrict__ rowptr,
@@ -53,31 +65,29 @@ __global__ void __launch_bounds__(RT) k_pcg_init(int64_t n, const int32_t* __res
   rz = block_sum(rz);
   bb = block_sum(bb);
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = rz;
-    part[RB + blockIdx.x] = bb;
+    part[RB + blockIdx.x] = rz;
+    part[2 * RB + blockIdx.x] = bb;
   }
 }
 
 __global__ void __launch_bounds__(RT) k_init_scalars(const double* __restrict__ part, Scalars* sc) {
-  double rz = 0.0, bb = 0.0;
-  for (int i = threadIdx.x; i < RB; i += RT) {
-    rz += part[i];
-    bb += part[RB + i];
-  }
-  rz = block_sum(rz);
-  bb = block_sum(bb);
+  const double rz = sum_partials(part, RB);
+  const double bb = sum_partials(part, 2 * RB);
   if (threadIdx.x == 0) {
     sc->rz = rz;
+    sc->rz_next = rz;
     sc->bb = bb;
     sc->rr = bb;
   }
 }
 
-// q = H p and the partial sums of p.q
+// q = H p and the partial sums of p.q.  Block 0 first publishes the r.z of the
+// previous iteration (read by k_update, which runs after this kernel).
 __global__ void __launch_bounds__(RT) k_spmv_dot(int64_t n, const int32_t* __restrict__ rowptr,
                                                  const int32_t* __restrict__ colind, const double* __restrict__ val,
                                                  const double* __restrict__ p, double* __restrict__ q,
-                                                 double* __restrict__ part) {
+                                                 double* __restrict__ part, Scalars* __restrict__ sc) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc->rz = sc->rz_next;
   double pq = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT) {
     double s = 0.0;
@@ -89,22 +99,24 @@ __global__ void __launch_bounds__(RT) k_spmv_dot(int64_t n, const int32_t* __res
   if (threadIdx.x == 0) part[blockIdx.x] = pq;
 }
 
-__global__ void __launch_bounds__(RT) k_alpha(const double* __restrict__ part, Scalars* sc) {
-  double pq = 0.0;
-  for (int i = threadIdx.x; i < RB; i += RT) pq += part[i];
-  pq = block_sum(pq);
-  if (threadIdx.x == 0) {
-    sc->pq = pq;
-    sc->alpha = pq > 0.0 ? sc->rz / pq : 0.0;
-  }
-}
-
-// x += alpha p, r -= alpha q, partial sums of r.z (z = dinv r) and r.r
+// alpha = r.z / p.q (every block reduces the p.q partials itself), then
+// x += alpha p, r -= alpha q, and the partial sums of r.z (z = dinv r), r.r.
 __global__ void __launch_bounds__(RT) k_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
                                                const double* __restrict__ p, const double* __restrict__ q,
-                                               const double* __restrict__ dinv, const Scalars* __restrict__ sc,
+                                               const double* __restrict__ dinv, Scalars* __restrict__ sc,
                                                double* __restrict__ part) {
-  const double alpha = sc->alpha;
+  __shared__ double s_alpha;
+  const double pq = sum_partials(part, 0);
+  if (threadIdx.x == 0) {
+    const double alpha = pq > 0.0 ? sc->rz / pq : 0.0;
+    s_alpha = alpha;
+    if (blockIdx.x == 0) {
+      sc->pq = pq;
+      sc->alpha = alpha;
+    }
+  }
+  __syncthreads();
+  const double alpha = s_alpha;
   double rz = 0.0, rr = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT) {
     x[i] = fma(alpha, p[i], x[i]);
@@ -116,32 +128,42 @@ __global__ void __launch_bounds__(RT) k_update(int64_t n, double* __restrict__ x
   rz = block_sum(rz);
   rr = block_sum(rr);
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = rz;
-    part[RB + blockIdx.x] = rr;
+    part[RB + blockIdx.x] = rz;
+    part[2 * RB + blockIdx.x] = rr;
   }
 }
 
-__global__ void __launch_bounds__(RT) k_beta(const double* __restrict__ part, Scalars* sc) {
-  double rz = 0.0, rr = 0.0;
-  for (int i = threadIdx.x; i < RB; i += RT) {
-    rz += part[i];
-    rr += part[RB + i];
-  }
-  rz = block_sum(rz);
-  rr = block_sum(rr);
-  if (threadIdx.x == 0) {
-    sc->beta = sc->rz > 0.0 ? rz / sc->rz : 0.0;
-    sc->rz = rz;
-    sc->rr = rr;
-  }
-}
-
-// p = dinv r + beta p
+// beta = r.z_new / r.z (every block reduces the partials itself; sc->rz is
+// only read here, the new value goes to sc->rz_next), then p = dinv r + beta p.
 __global__ void __launch_bounds__(RT) k_direction(int64_t n, double* __restrict__ p, const double* __restrict__ r,
-                                                  const double* __restrict__ dinv, const Scalars* __restrict__ sc) {
-  const double beta = sc->beta;
+                                                  const double* __restrict__ dinv, Scalars* __restrict__ sc,
+                                                  const double* __restrict__ part) {
+  __shared__ double s_beta;
+  const double rz = sum_partials(part, RB);
+  const double rr = sum_partials(part, 2 * RB);
+  if (threadIdx.x == 0) {
+    const double rz_old = sc->rz;
+    s_beta = rz_old > 0.0 ? rz / rz_old : 0.0;
+    if (blockIdx.x == 0) {
+      sc->beta = s_beta;
+      sc->rr = rr;
+      sc->rz_next = rz;
+    }
+  }
+  __syncthreads();
+  const double beta = s_beta;
   for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT)
     p[i] = fma(beta, p[i], dinv[i] * r[i]);
+}
+
+// one PCG iteration: 3 launches
+inline cudaError_t pcg_iteration(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* values,
+                                 double* x, double* r, double* p, double* q, const double* dinv, double* part,
+                                 Scalars* sc, cudaStream_t s) {
+  k_spmv_dot<<<RB, RT, 0, s>>>(n, rowptr, colind, values, p, q, part, sc);
+  k_update<<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
+  k_direction<<<RB, RT, 0, s>>>(n, p, r, dinv, sc, part);
+  return ph::launched(3);
 }
 
 }  // namespace
@@ -159,12 +181,11 @@ extern "C" ph_status ph_solve_pcg(int64_t n, const int32_t* rowptr, const int32_
   cudaStream_t s = (cudaStream_t)stream;
   double* work = nullptr;
   const size_t nvec = (size_t)n;
-  // r, p, q, dinv, partial sums (2 RB), scalars, flag
-  const size_t bytes = sizeof(double) * (4 * nvec + 2 * RB) + sizeof(Scalars) + 16;
+  const size_t bytes = sizeof(double) * (4 * nvec + kPart) + sizeof(Scalars) + 16;
   cudaError_t e = alloc_bytes(reinterpret_cast<void**>(&work), bytes, s);
   if (e != cudaSuccess) return cuda_status(e, "pcg alloc");
   double *r = work, *p = r + nvec, *q = p + nvec, *dinv = q + nvec, *part = dinv + nvec;
-  Scalars* sc = reinterpret_cast<Scalars*>(part + 2 * RB);
+  Scalars* sc = reinterpret_cast<Scalars*>(part + kPart);
   unsigned* bad = reinterpret_cast<unsigned*>(sc + 1);
   ph_status st = PH_OK;
   Scalars h;
@@ -189,14 +210,8 @@ extern "C" ph_status ph_solve_pcg(int64_t n, const int32_t* rowptr, const int32_
   res = bnorm;
   while (res > rtol * bnorm && it < maxit) {
     const int batch = (maxit - it) < 8 ? (maxit - it) : 8;
-    for (int i = 0; i < batch && e == cudaSuccess; ++i) {
-      k_spmv_dot<<<RB, RT, 0, s>>>(n, rowptr, colind, values, p, q, part);
-      k_alpha<<<1, RT, 0, s>>>(part, sc);
-      k_update<<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
-      k_beta<<<1, RT, 0, s>>>(part, sc);
-      k_direction<<<RB, RT, 0, s>>>(n, p, r, dinv, sc);
-      e = launched(5);
-    }
+    for (int i = 0; i < batch && e == cudaSuccess; ++i)
+      e = pcg_iteration(n, rowptr, colind, values, x, r, p, q, dinv, part, sc, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { st = cuda_status(e, "pcg"); goto done; }
@@ -212,6 +227,25 @@ done:
   return st;
 }
 
+// y = H x
+__global__ void k_spmv(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                       const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int j = rowptr[i]; j < rowptr[i + 1]; ++j) s = fma(val[j], x[colind[j]], s);
+  y[i] = s;
+}
+
+extern "C" ph_status ph_spmv(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* values,
+                             const double* x, double* y, void* stream) {
+  if (n < 0) return PH_ERR_ARG;
+  if (n == 0) return PH_OK;
+  if (!rowptr || !colind || !values || !x || !y) return PH_ERR_ARG;
+  k_spmv<<<grid_for(n), kThreads, 0, (cudaStream_t)stream>>>(n, rowptr, colind, values, x, y);
+  return cuda_status(launched(), "ph_spmv");
+}
+
 // ---------------------------------------------------------------------------
 // ph_solve_pcg_noalloc: the iteration above with its workspace in a fixed
 // device array instead of the library's pool, for callers that must not
@@ -221,9 +255,8 @@ done:
 
 #include <mutex>
 
-// r, p, q, dinv (4 n doubles), partial sums (2 RB), scalars and the flag word.
-static constexpr size_t kNoAllocDoubles =
-    4 * (size_t)PH_PCG_NOALLOC_MAX_N + 2 * (size_t)RB + (sizeof(Scalars) + 16 + 7) / 8;
+// r, p, q, dinv (4 n doubles), partial sums, scalars and the flag word.
+static constexpr size_t kNoAllocDoubles = 4 * (size_t)PH_PCG_NOALLOC_MAX_N + kPart + (sizeof(Scalars) + 16 + 7) / 8;
 static __device__ __align__(256) double g_pcg_noalloc_work[kNoAllocDoubles];
 
 static std::mutex g_noalloc_mu;
@@ -265,7 +298,7 @@ extern "C" ph_status ph_solve_pcg_noalloc(int64_t n, const int32_t* rowptr, cons
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nvec = (size_t)n;
   double *r = work, *p = r + nvec, *q = p + nvec, *dinv = q + nvec, *part = dinv + nvec;
-  Scalars* sc = reinterpret_cast<Scalars*>(part + 2 * RB);
+  Scalars* sc = reinterpret_cast<Scalars*>(part + kPart);
   unsigned* bad = reinterpret_cast<unsigned*>(sc + 1);
   Scalars h;
   unsigned hbad = 0;
@@ -289,14 +322,8 @@ extern "C" ph_status ph_solve_pcg_noalloc(int64_t n, const int32_t* rowptr, cons
   res = bnorm;
   while (res > rtol * bnorm && it < maxit) {
     const int batch = (maxit - it) < 8 ? (maxit - it) : 8;
-    for (int i = 0; i < batch && e == cudaSuccess; ++i) {
-      k_spmv_dot<<<RB, RT, 0, s>>>(n, rowptr, colind, values, p, q, part);
-      k_alpha<<<1, RT, 0, s>>>(part, sc);
-      k_update<<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
-      k_beta<<<1, RT, 0, s>>>(part, sc);
-      k_direction<<<RB, RT, 0, s>>>(n, p, r, dinv, sc);
-      e = launched(5);
-    }
+    for (int i = 0; i < batch && e == cudaSuccess; ++i)
+      e = pcg_iteration(n, rowptr, colind, values, x, r, p, q, dinv, part, sc, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e, "ph_solve_pcg_noalloc");
