@@ -339,9 +339,135 @@ def gpu_arm(args, rank, world, local_rank):
         "clocks": clk,
         "setup": {"host_mesh_generation_s": gen_s},
     }
+    if not args.no_extras:
+        line["batched"] = batched_section(ph, dev, steps=max(3, args.steps // 10), warmup=3)
+        line["adjoint"] = adjoint_section(ph, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, budget_s=args.cpu_budget)
     return line
+
+
+# ---------------------------------------------------------------------------
+# batched workload: 256 problems, Kuhn m_i^3 cubes refined once, m_i from
+# sizes log-uniform in [1e4, 5e5] elements (seed 4), each its own lognormal a
+# ---------------------------------------------------------------------------
+def batched_section(ph, dev, steps, warmup):
+    import torch
+    rng = np.random.Generator(np.random.PCG64(4))
+    sizes = np.exp(rng.uniform(np.log(1e4), np.log(5e5), 256))
+    ms = np.clip(np.round((sizes / 72.0) ** (1.0 / 3.0)), 6, 19).astype(int)
+    cache = {}
+    probs = []
+    for i, m in enumerate(ms):
+        if m not in cache:
+            coord, tet = meshgen.kuhn_cube(int(m))
+            coord, tet, _ = meshgen.refined(coord, tet, 1)
+            mesh = ph.Mesh(torch.as_tensor(coord, device=dev), torch.as_tensor(tet, device=dev))
+            cen = mesh.faces()["face_centroid"].cpu().numpy()
+            f = torch.as_tensor(np.asarray(meshgen.sin_source(cen), np.float64), device=dev)
+            cache[m] = (mesh, f)
+        mesh, f = cache[m]
+        a = torch.as_tensor(meshgen.lognormal_field(mesh.nE, 4000 + i), device=dev)
+        probs.append(dict(mesh=mesh, f=f, a=a,
+                          values=torch.empty(mesh.nnz, dtype=torch.float64, device=dev),
+                          rhs=torch.empty(mesh.L, dtype=torch.float64, device=dev),
+                          factor=torch.empty((mesh.nE, 10), dtype=torch.float64, device=dev)))
+    total = sum(p["mesh"].nE for p in probs)
+    batch = ph.Batch([p["mesh"] for p in probs])
+    batch.bind([p["a"] for p in probs], [0.1] * len(probs), [p["f"] for p in probs], [p["values"] for p in probs],
+               [p["rhs"] for p in probs], factor=[p["factor"] for p in probs])
+    tune_ms = batch.autotune(reps=2)
+    cfg = dict(batch.get_config(), best_ms=tune_ms)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    n0 = ph.ph_launch_count()
+    graph_ms = timed(batch.graph_launch)
+    launches_graph = (ph.ph_launch_count() - n0) / (steps + warmup)
+
+    def plain():
+        for p in probs:
+            p["mesh"].assemble(p["a"], 0.1, p["f"], values=p["values"], rhs=p["rhs"], factor=p["factor"])
+
+    n0 = ph.ph_launch_count()
+    plain_ms = timed(plain)
+    launches_plain = (ph.ph_launch_count() - n0) / (steps + warmup)
+    batch.close()
+    return {
+        "problems": len(probs), "tets": int(total), "distinct_meshes": len(cache),
+        "batched_graph_ms": graph_ms, "batched_tets_per_s": total / (graph_ms * 1e-3),
+        "plain_sequential_ms": plain_ms, "plain_sequential_tets_per_s": total / (plain_ms * 1e-3),
+        "speedup_vs_sequential": plain_ms / graph_ms, "autotuned": cfg,
+        "launches_per_batch": {"graph": launches_graph, "sequential": launches_plain},
+    }
+
+
+# ---------------------------------------------------------------------------
+# adjoint workload: Kuhn 6^3 cube refined 3 levels (2,239,488 tets), c = 0.1,
+# U_obs from a lognormal a (seed 5), gradient at a lognormal a (seed 51)
+# ---------------------------------------------------------------------------
+def adjoint_section(ph, dev, rtol=1e-10):
+    import torch
+    p = meshgen.problem("kuhn_m6_k3")
+    mesh = ph.Mesh(torch.as_tensor(p.coord, device=dev), torch.as_tensor(p.tet, device=dev))
+    cen = mesh.faces()["face_centroid"].cpu().numpy()
+    f = torch.as_tensor(np.asarray(meshgen.sin_source(cen), np.float64), device=dev)
+    rowptr, colind = mesh.csr_pattern()
+    c = 0.1
+
+    def forward(a):
+        values, rhs, factor = mesh.assemble(a, c, f, factor=True)
+        lam, it, rr, _ = ph.ph_solve_pcg(rowptr, colind, values, rhs, rtol=rtol, maxit=200000, check=False)
+        u = mesh.recover_factored(factor, c, f, lam)
+        return values, factor, u, it
+
+    a_obs = torch.as_tensor(meshgen.lognormal_field(p.nE, 5), device=dev)
+    u_obs = forward(a_obs)[2]
+    a = torch.as_tensor(meshgen.lognormal_field(p.nE, 51), device=dev)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    values, rhs, factor = mesh.assemble(a, c, f, factor=True)
+    ev[1].record(stream)
+    lam, it1, _, _ = ph.ph_solve_pcg(rowptr, colind, values, rhs, rtol=rtol, maxit=200000, check=False)
+    ev[2].record(stream)
+    u = mesh.recover_factored(factor, c, f, lam)
+    J = mesh.misfit(u, u_obs)
+    ev[3].record(stream)
+    rq = mesh.adjoint_rhs(factor, c, u, u_obs)
+    ev[4].record(stream)
+    q, it2, _, _ = ph.ph_solve_pcg(rowptr, colind, values, rq, rtol=rtol, maxit=200000, check=False)
+    ev[5].record(stream)
+    grad = mesh.adjoint_grad(a, factor, c, u, u_obs, q)
+    ev[6].record(stream)
+    torch.cuda.synchronize()
+    t = [ev[i].elapsed_time(ev[i + 1]) for i in range(6)]
+    total = sum(t)
+    adj_kernels_ms = t[3] + t[5]
+    out = {
+        "workload": "Kuhn 6^3 cube, 3 refinement levels", "nE": p.nE, "L": mesh.L,
+        "J": J.item(), "grad_norm": grad.norm().item(),
+        "grads_per_s": 1000.0 / total, "ms_per_gradient": total,
+        "ms": {"assemble": t[0], "forward_solve": t[1], "recover_misfit": t[2], "adjoint_rhs": t[3],
+               "adjoint_solve": t[4], "adjoint_grad": t[5]},
+        "pcg_iterations": [it1, it2], "pcg_rtol": rtol,
+        "adjoint_kernels_tets_per_s": p.nE / (adj_kernels_ms * 1e-3),
+        "note": "gradient time is dominated by the two Jacobi-PCG solves of the condensed system",
+    }
+    mesh.close()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -435,6 +561,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiler runs)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint sections")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=3.0)

@@ -223,6 +223,42 @@ ph_status ph_solve_pcg_noalloc(int64_t n, const int32_t* rowptr, const int32_t* 
                                double* relres, void* stream);
 
 /*
+ * Batched assembly (not in the paper): many problems, meshes of uneven size
+ * each with its own coefficient field, assembled and condensed by one
+ * persistent kernel (plus one kernel that clears the entries receiving atomic
+ * contributions).  Each problem's values, rhs and factor are bit-identical to
+ * a plain ph_assemble call on it.  A batch is not thread-safe.
+ *   ph_batch_create   group n meshes (the meshes must outlive the batch).
+ *   ph_batch_bind     per-problem arrays: host arrays of n DEVICE pointers
+ *                     (uD_face, gN_face, factor may be NULL arrays or hold
+ *                     NULL entries) and a host array c[n]; uploads a
+ *                     descriptor table and synchronises `stream`.
+ *   ph_batch_assemble enqueue the two kernels; no allocation, no
+ *                     synchronisation (capturable).
+ *   ph_batch_autotune time the candidate configurations (tiles of 256..16384
+ *                     elements, 64..256 threads, 2..8 blocks per SM) `reps`
+ *                     times each on the bound problems, keep the fastest and
+ *                     return its time per batch in *best_ms (host).
+ *   ph_batch_set_config / ph_batch_get_config  the configuration in use.
+ *   ph_batch_graph_launch  on first use, capture the two launches into a CUDA
+ *                     graph (instantiated once; ph_batch_set_config and the
+ *                     autotuner reset it, ph_batch_bind keeps it valid since
+ *                     it rewrites the descriptor table in place), then launch
+ *                     the graph on `stream`.
+ */
+typedef struct ph_batch ph_batch;
+ph_status ph_batch_create(ph_mesh* const* meshes, int32_t n, void* stream, ph_batch** out);
+ph_status ph_batch_destroy(ph_batch* batch, void* stream);
+ph_status ph_batch_bind(ph_batch* batch, const double* const* a, const double* c, const double* const* f_face,
+                        const double* const* uD_face, const double* const* gN_face, double* const* values,
+                        double* const* rhs, double* const* factor, void* stream);
+ph_status ph_batch_assemble(ph_batch* batch, void* stream);
+ph_status ph_batch_autotune(ph_batch* batch, int32_t reps, float* best_ms, void* stream);
+ph_status ph_batch_set_config(ph_batch* batch, int32_t tile, int32_t threads, int32_t blocks_per_sm, void* stream);
+ph_status ph_batch_get_config(const ph_batch* batch, int32_t* tile, int32_t* threads, int32_t* blocks_per_sm);
+ph_status ph_batch_graph_launch(ph_batch* batch, void* stream);
+
+/*
  * y = H x for a CSR matrix (rowptr [n+1], colind, values) and x [n], y [n]
  * (float64 device arrays).  One kernel, no synchronisation.
  */

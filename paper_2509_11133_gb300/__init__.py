@@ -30,7 +30,9 @@ STATUS_NAMES = {0: "PH_OK", 1: "PH_ERR_ARG", 2: "PH_ERR_DEGENERATE", 3: "PH_ERR_
 EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces", "ph_csr_pattern", "ph_assemble",
            "ph_recover", "ph_solve_pcg", "ph_mesh_check", "ph_status_string", "ph_last_error_message",
            "ph_launch_count", "ph_solve_pcg_noalloc", "ph_recover_factored", "ph_spmv", "ph_misfit",
-           "ph_adjoint_rhs", "ph_adjoint_grad")
+           "ph_adjoint_rhs", "ph_adjoint_grad", "ph_batch_create", "ph_batch_destroy", "ph_batch_bind",
+           "ph_batch_assemble", "ph_batch_autotune", "ph_batch_set_config", "ph_batch_get_config",
+           "ph_batch_graph_launch")
 
 
 class PHError(RuntimeError):
@@ -76,6 +78,14 @@ def load(path: str | None = None):
         "ph_misfit": [P, P, P, P, P],
         "ph_adjoint_rhs": [P, P, D, P, P, P, P],
         "ph_adjoint_grad": [P, P, P, D, P, P, P, P, P],
+        "ph_batch_create": [P, I32, P, ctypes.POINTER(P)],
+        "ph_batch_destroy": [P, P],
+        "ph_batch_bind": [P, P, P, P, P, P, P, P, P, P],
+        "ph_batch_assemble": [P, P],
+        "ph_batch_autotune": [P, I32, ctypes.POINTER(ctypes.c_float), P],
+        "ph_batch_set_config": [P, I32, I32, I32, P],
+        "ph_batch_get_config": [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)],
+        "ph_batch_graph_launch": [P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -311,6 +321,78 @@ class Mesh:
 
 def ph_mesh_create(coord, tet, neumann=None, stream=None) -> Mesh:
     return Mesh(coord, tet, neumann, stream)
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * max(len(tensors), 1))()
+    for i, t in enumerate(tensors):
+        arr[i] = None if t is None else t.data_ptr()
+    return arr
+
+
+class Batch:
+    """A batch of meshes assembled by one persistent kernel (ph_batch_*).
+
+    bind() takes per-problem lists of CUDA tensors (outputs included); the
+    lists are kept alive by the Batch while bound."""
+
+    def __init__(self, meshes, stream=None):
+        self.meshes = list(meshes)
+        h = ctypes.c_void_p()
+        handles = (ctypes.c_void_p * max(len(self.meshes), 1))(*[m.handle.value for m in self.meshes])
+        self._h = None
+        _check(load().ph_batch_create(handles, len(self.meshes), _stream(stream), ctypes.byref(h)), "ph_batch_create")
+        self._h = h
+        self._bound = None
+
+    def bind(self, a, c, f_face, values, rhs, factor=None, uD_face=None, gN_face=None, stream=None):
+        n = len(self.meshes)
+        for m, aa, ff, vv, rr in zip(self.meshes, a, f_face, values, rhs):
+            _need(aa, torch.float64, m.nE, "a")
+            _need(ff, torch.float64, m.nF, "f_face")
+            _need(vv, torch.float64, m.nnz, "values")
+            _need(rr, torch.float64, m.L, "rhs")
+        if factor is not None:
+            for m, fa in zip(self.meshes, factor):
+                if fa is not None:
+                    _need(fa, torch.float64, 10 * m.nE, "factor")
+        cs = (ctypes.c_double * max(n, 1))(*[float(x) for x in c])
+        arrs = [_ptr_array(x) if x is not None else None for x in (a, f_face, uD_face, gN_face, values, rhs, factor)]
+        _check(load().ph_batch_bind(self._h, arrs[0], cs, arrs[1], arrs[2], arrs[3], arrs[4], arrs[5], arrs[6],
+                                    _stream(stream)), "ph_batch_bind")
+        self._bound = (a, c, f_face, values, rhs, factor, uD_face, gN_face)
+
+    def assemble(self, stream=None):
+        _check(load().ph_batch_assemble(self._h, _stream(stream)), "ph_batch_assemble")
+
+    def graph_launch(self, stream=None):
+        _check(load().ph_batch_graph_launch(self._h, _stream(stream)), "ph_batch_graph_launch")
+
+    def autotune(self, reps=3, stream=None):
+        ms = ctypes.c_float(0)
+        _check(load().ph_batch_autotune(self._h, int(reps), ctypes.byref(ms), _stream(stream)), "ph_batch_autotune")
+        return ms.value
+
+    def set_config(self, tile, threads, blocks_per_sm, stream=None):
+        _check(load().ph_batch_set_config(self._h, tile, threads, blocks_per_sm, _stream(stream)),
+               "ph_batch_set_config")
+
+    def get_config(self):
+        t, th, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().ph_batch_get_config(self._h, ctypes.byref(t), ctypes.byref(th), ctypes.byref(b)),
+               "ph_batch_get_config")
+        return {"tile": t.value, "threads": th.value, "blocks_per_sm": b.value}
+
+    def close(self, stream=None):
+        if self._h is not None:
+            load().ph_batch_destroy(self._h, _stream(stream))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class MisfitFunction(torch.autograd.Function):

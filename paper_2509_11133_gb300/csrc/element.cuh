@@ -67,4 +67,94 @@ __device__ __forceinline__ void face_kernel(const Geo& G, double a, double c20, 
 
 __device__ __forceinline__ double neg_if(double x, bool n) { return n ? -x : x; }
 
+
+// Local matrices, condensation and scatter of element t (Section 4.2-4.3,
+// Eq. schur): the body of the assembly kernels (one thread per element).
+template <bool UD, bool GN, bool FAC>
+__device__ __forceinline__ void assemble_element(int64_t t, const double* __restrict__ geo,
+                                                 const int4* __restrict__ tface, const int4* __restrict__ tmult,
+                                                 const int4* __restrict__ tpos, const ushort4* __restrict__ trel,
+                                                 const double* __restrict__ face_area, const double* __restrict__ a,
+                                                 double c20, double six_over_c, const double* __restrict__ f_face,
+                                                 const double* __restrict__ uD, const double* __restrict__ gN,
+                                                 double* __restrict__ values, double* __restrict__ rhs,
+                                                 double* __restrict__ factor, unsigned* status) {
+  const double at = __ldg(a + t);
+  if (!(at > 0.0) || !(at < INFINITY)) {
+    ph_flag(status, PH_ERR_ARG);
+    return;
+  }
+  const Geo G = load_geo(geo, t);
+  const int4 tf = __ldg(tface + t);
+  const int4 tm = __ldg(tmult + t);
+  int F[4];
+  bool neg[4];
+  double ar[4], h[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    F[k] = comp(tf, k) & PH_ID_MASK;
+    neg[k] = comp(tf, k) < 0;
+    ar[k] = __ldg(face_area + F[k]);
+  }
+  const double q4 = G.adet * (1.0 / 24.0);  // |T| / 4
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    h[k] = q4 * __ldg(f_face + F[k]);
+    if (GN && comp(tm, k) == PH_NO_MULT) h[k] = fma(ar[k], __ldg(gN + F[k]), h[k]);
+  }
+  double Q[10];
+  face_kernel(G, at, c20, 6.0 / 9.0, Q);
+  if (FAC) {
+    double2* fo = reinterpret_cast<double2*>(factor + 10 * t);
+    fo[0] = make_double2(Q[0], Q[1]);
+    fo[1] = make_double2(Q[2], Q[3]);
+    fo[2] = make_double2(Q[4], Q[5]);
+    fo[3] = make_double2(Q[6], Q[7]);
+    fo[4] = make_double2(Q[8], Q[9]);
+  }
+  const double icT = G.rdet * six_over_c;  // 1/(c|T|)
+  const double hs = (h[0] + h[1]) + (h[2] + h[3]);
+  const double base = icT * hs;
+  // condensed block S[k][m] = d_k d_m (1/(c|T|) + Qf/9), each entry once
+  double S[10];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int m = k; m < 4; ++m) S[ut(k, m)] = neg_if((ar[k] * ar[m]) * (icT + Q[ut(k, m)]), neg[k] != neg[m]);
+  const int4 tp = __ldg(tpos + t);
+  const ushort4 tr = __ldg(trel + t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int mk = comp(tm, k);
+    if (mk == PH_NO_MULT) continue;
+    const int l = mk & PH_ID_MASK;
+    const bool bnd = mk < 0;
+    // g_k = -d_k (h'sum/(c|T|) + (Qf h')_k / 9)
+    double e = base;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) e = fma(Q[ut(k, m)], h[m], e);
+    double g = neg_if(-ar[k] * e, neg[k]);
+    if (UD && bnd) g = fma(ar[k], __ldg(uD + F[k]), g);  // b_D = |F| u_D(Ct_F)
+    const int pd = comp(tp, k);
+    if (bnd) {
+      values[pd] = S[ut(k, k)];
+      rhs[l] = g;
+    } else {
+      atomicAdd(values + pd, S[ut(k, k)]);
+      atomicAdd(rhs + l, g);
+    }
+    const unsigned rel = comps(tr, k);
+    int idx = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if (m == k) continue;
+      if (comp(tm, m) != PH_NO_MULT) {
+        const int off = ((int)(rel << (28 - 4 * idx))) >> 28;  // sign-extend 4 bits
+        values[pd + off] = S[ut(k, m)];
+      }
+      ++idx;
+    }
+  }
+}
+
 }  // namespace ph_elem

@@ -1,0 +1,141 @@
+"""Batched assembly (one persistent launch over many meshes of uneven size,
+each with its own coefficient field) against plain per-problem ph_assemble
+calls: values, rhs and element factor must be bit-identical, under every
+configuration the autotuner tries, and through the captured CUDA graph."""
+import numpy as np
+import pytest
+
+import meshgen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ph():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2509_11133_gb300 as ph
+    from paper_2509_11133_gb300 import build
+    build.build()
+    ph.load()
+    return ph
+
+
+def cu(x):
+    return torch.as_tensor(np.ascontiguousarray(x), device="cuda")
+
+
+def problems():
+    out = []
+    for i, (m, k) in enumerate([(1, 0), (2, 1), (1, 2), (3, 1), (6, 1), (2, 2), (5, 1)]):
+        coord, tet = meshgen.kuhn_cube(m)
+        coord, tet, _ = meshgen.refined(coord, tet, k)
+        out.append(meshgen.Problem(f"k{m}_{k}", coord, tet, meshgen.lognormal_field(tet.shape[0], 4000 + i),
+                                   0.1 + 0.05 * i, lambda x: meshgen.sin_source(x)))
+    out.append(meshgen.problem("paper_mixed", 2))          # Neumann faces and Dirichlet data
+    coord, tet = meshgen.shuffled(out[1].coord, out[1].tet, 3)
+    out.append(meshgen.Problem("shuffled", coord, tet, meshgen.lognormal_field(tet.shape[0], 9), 0.7, out[1].f))
+    return out
+
+
+class Case:
+    def __init__(self, ph, p):
+        neu = cu(p.neumann.astype(np.int32)) if p.neumann.size else None
+        self.mesh = ph.Mesh(cu(p.coord), cu(p.tet.astype(np.int32)), neu)
+        cen = self.mesh.faces()["face_centroid"].cpu().numpy()
+        self.f = cu(np.asarray(p.f(cen), np.float64))
+        self.uD = None if p.uD is None else cu(np.asarray(p.uD(cen), np.float64))
+        self.gN = None if p.gN is None else cu(np.asarray(p.gN(cen), np.float64))
+        self.a = cu(p.a)
+        self.c = p.c
+        m = self.mesh
+        self.values = torch.full((m.nnz,), np.nan, dtype=torch.float64, device="cuda")
+        self.rhs = torch.full((m.L,), np.nan, dtype=torch.float64, device="cuda")
+        self.factor = torch.full((m.nE, 10), np.nan, dtype=torch.float64, device="cuda")
+        self.ref = m.assemble(self.a, self.c, self.f, self.uD, self.gN, factor=True)
+
+
+@pytest.fixture(scope="module")
+def batch(ph):
+    cases = [Case(ph, p) for p in problems()]
+    b = ph.Batch([c.mesh for c in cases])
+    b.bind([c.a for c in cases], [c.c for c in cases], [c.f for c in cases], [c.values for c in cases],
+           [c.rhs for c in cases], factor=[c.factor for c in cases], uD_face=[c.uD for c in cases],
+           gN_face=[c.gN for c in cases])
+    return b, cases
+
+
+def assert_identical(cases):
+    torch.cuda.synchronize()
+    for c in cases:
+        v, r, f = c.ref
+        assert torch.equal(c.values, v)
+        assert torch.equal(c.rhs, r)
+        assert torch.equal(c.factor, f)
+        c.mesh.check()
+
+
+def _reset(cases):
+    for c in cases:
+        c.values.fill_(np.nan)
+        c.rhs.fill_(np.nan)
+        c.factor.fill_(np.nan)
+
+
+def test_batched_equals_plain(batch):
+    b, cases = batch
+    _reset(cases)
+    b.assemble()
+    assert_identical(cases)
+
+
+@pytest.mark.parametrize("cfg", [(256, 64, 2), (1024, 128, 4), (4096, 256, 8), (16384, 128, 1), (32, 32, 32)])
+def test_every_configuration(batch, cfg):
+    b, cases = batch
+    b.set_config(*cfg)
+    assert tuple(b.get_config().values()) == cfg
+    _reset(cases)
+    b.assemble()
+    assert_identical(cases)
+
+
+def test_autotune_and_graph(batch):
+    b, cases = batch
+    ms = b.autotune(reps=2)
+    assert ms > 0
+    cfg = b.get_config()
+    assert cfg["tile"] in (256, 1024, 4096, 16384)
+    for _ in range(2):
+        _reset(cases)
+        b.graph_launch()
+        assert_identical(cases)
+    # rebinding new coefficients keeps the graph valid and changes the result
+    for c in cases:
+        c.a.mul_(1.5)
+        c.ref = c.mesh.assemble(c.a, c.c, c.f, c.uD, c.gN, factor=True)
+    _reset(cases)
+    b.graph_launch()
+    assert_identical(cases)
+
+
+def test_config4_recipe_subset(ph):
+    """16 problems drawn like the batched workload (sizes log-uniform in
+    [1e4, 5e5] elements, each its own lognormal field)."""
+    rng = np.random.Generator(np.random.PCG64(4))
+    sizes = np.exp(rng.uniform(np.log(1e4), np.log(5e5), 16))
+    cases = []
+    for i, s in enumerate(sizes):
+        m = int(np.clip(round((s / 72) ** (1 / 3)), 6, 19))
+        coord, tet = meshgen.kuhn_cube(m)
+        coord, tet, _ = meshgen.refined(coord, tet, 1)
+        p = meshgen.Problem("b", coord, tet, meshgen.lognormal_field(tet.shape[0], 4000 + i), 0.1,
+                            lambda x: meshgen.sin_source(x))
+        cases.append(Case(ph, p))
+    b = ph.Batch([c.mesh for c in cases])
+    b.bind([c.a for c in cases], [c.c for c in cases], [c.f for c in cases], [c.values for c in cases],
+           [c.rhs for c in cases], factor=[c.factor for c in cases])
+    b.autotune(reps=1)
+    b.graph_launch()
+    assert_identical(cases)
+    b.close()
