@@ -71,8 +71,9 @@ __global__ void k_face_count(const int4* __restrict__ tet, int64_t nE, int64_t n
   }
 }
 
-// 2. scatter keys into buckets: entry = (v0, v1, v2, slot), slot = 4t+k for
-//    tet faces and 4nE+i for Neumann triples.  cnt counts down to 0.
+// 2. scatter keys into buckets (all keys of a bucket share v2): entry =
+//    (v0, v1, v2, slot), slot = 4t+k for tet faces and 4nE+i for Neumann
+//    triples.  cnt counts down to 0.
 __global__ void k_face_fill(const int4* __restrict__ tet, int64_t nE, int64_t nC, const int32_t* __restrict__ nb,
                             int64_t nN, const int32_t* __restrict__ start, int32_t* __restrict__ cnt,
                             int4* __restrict__ entries) {
@@ -91,7 +92,29 @@ __global__ void k_face_fill(const int4* __restrict__ tet, int64_t nE, int64_t nC
     if (!valid_tri(f, nC)) return;
     int3 s = sort3(f);
     int pos = start[s.z] + atomicSub(&cnt[s.z], 1) - 1;
-    entries[pos] = make_int4(s.x, s.y, s.z, (int)i + 3 * (int)nE);  // = 4nE + (i - nE)
+    entries[pos] = make_int4(s.x, s.y, s.z, (int)i + 3 * (int)nE);  // slot 4nE + (i - nE)
+  }
+}
+
+// Scan entries[j0, j1) for (v0, v1) == (e.x, e.y) (v2 is the bucket's);
+// counts tet and Neumann matches.  Four independent loads per step.
+__device__ __forceinline__ void scan_bucket(const int4* __restrict__ entries, int j0, int j1, int skip, int4 e,
+                                            int64_t ntet, int& nt, int& nn, int& tm) {
+  int j = j0;
+  for (; j + 3 < j1; j += 4) {
+    const int4 k0 = entries[j], k1 = entries[j + 1], k2 = entries[j + 2], k3 = entries[j + 3];
+    const int4 kk[4] = {k0, k1, k2, k3};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (kk[u].x == e.x && kk[u].y == e.y && j + u != skip) {
+        if (kk[u].w < ntet) { ++nt; tm = kk[u].w; } else { ++nn; }
+      }
+  }
+  for (; j < j1; ++j) {
+    const int4 k = entries[j];
+    if (k.x == e.x && k.y == e.y && j != skip) {
+      if (k.w < ntet) { ++nt; tm = k.w; } else { ++nn; }
+    }
   }
 }
 
@@ -105,19 +128,14 @@ __global__ void k_face_fill(const int4* __restrict__ tet, int64_t nE, int64_t nC
 //    entry.
 __global__ void k_face_match(const int4* __restrict__ entries, int64_t nent, const int32_t* __restrict__ start,
                              int64_t nE, int32_t* __restrict__ mate, unsigned* status) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nent) return;
   const int4 e = entries[i];
-  const int lo = start[e.z], hi = start[e.z + 1];
+  const int hi = start[e.z + 1];
   const int64_t ntet = 4 * nE;
+  int nt = 0, nn = 0, tm = -1;
   if (e.w < ntet) {
-    int nt = 0, nn = 0, tm = -1;
-    for (int j = (int)i + 1; j < hi; ++j) {
-      const int4 f = entries[j];
-      if (f.x == e.x && f.y == e.y) {
-        if (f.w < ntet) { ++nt; tm = f.w; } else { ++nn; }
-      }
-    }
+    scan_bucket(entries, (int)i + 1, hi, -1, e, ntet, nt, nn, tm);
     if (nt + nn >= 2) ph_flag(status, nn > 0 ? PH_ERR_ARG : PH_ERR_NONMANIFOLD);
     if (nt == 1) {
       mate[e.w] = tm;
@@ -126,14 +144,7 @@ __global__ void k_face_match(const int4* __restrict__ entries, int64_t nent, con
       mate[e.w] = -2;
     }
   } else {
-    int nt = 0, nn = 0, tm = -1;
-    for (int j = lo; j < hi; ++j) {
-      if (j == i) continue;
-      const int4 f = entries[j];
-      if (f.x == e.x && f.y == e.y) {
-        if (f.w < ntet) { ++nt; tm = f.w; } else { ++nn; }
-      }
-    }
+    scan_bucket(entries, start[e.z], hi, (int)i, e, ntet, nt, nn, tm);
     if (nt != 1 || nn != 0) ph_flag(status, PH_ERR_ARG);
     else mate[tm] = -2;
   }
