@@ -137,6 +137,25 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# ranks
+# ---------------------------------------------------------------------------
+def max_over_ranks(values, world, device):
+    """Element-wise maximum of per-rank timings (all ranks get the result)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all ranks per second, timed by the slowest rank."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def make_problem(name):
@@ -274,12 +293,7 @@ def gpu_arm(args, rank, world, local_rank):
     e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in ee])) if ee else float("nan")
 
     # max over ranks
-    if world > 1:
-        t = torch.tensor([ms_per_step, e2e_ms, float(np.mean(asm_ms))], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step, e2e_ms, asm_max = (float(x) for x in t.tolist())
-    else:
-        asm_max = float(np.mean(asm_ms))
+    ms_per_step, e2e_ms, asm_max = max_over_ranks([ms_per_step, e2e_ms, float(np.mean(asm_ms))], world, dev)
 
     if rank != 0:
         return None
@@ -290,7 +304,7 @@ def gpu_arm(args, rank, world, local_rank):
     achieved_gops = ops / asm_s / 1e9
     traffic = profile_traffic()
     bpt = assemble_bytes_per_tet(nE, p.nC, nF)
-    value = world * nE / (ms_per_step * 1e-3)
+    value = whole_job_rate(nE, world, ms_per_step)
     line = {
         "metric": METRIC,
         "value": value,
@@ -332,7 +346,7 @@ def gpu_arm(args, rank, world, local_rank):
             "frac": bpt * nE / asm_s / 1e9 / hbm_peak, "bytes_per_tet": bpt,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
         },
-        "e2e": None if args.no_e2e else {"value": world * nE / (e2e_ms * 1e-3), "unit": UNIT,
+        "e2e": None if args.no_e2e else {"value": whole_job_rate(nE, world, e2e_ms), "unit": UNIT,
                                          "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": int(n_launch),
         "gpu_launches_per_step": n_launch / args.steps,

@@ -58,30 +58,53 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def _configure(L):
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    D = ctypes.c_double
+    L.or_faces.argtypes = [I64, I64, P, I64, P, P, P, P, P, P]
+    L.or_multipliers.argtypes = [I64, P, P, P]
+    L.or_csr_pattern.argtypes = [I64, P, P, I64, P, P, P]
+    L.or_face_centroids.argtypes = [I64, P, P, P]
+    L.or_tet_local.argtypes = [P, D, D, P, P, P, P, P, P]
+    L.or_tet_matrices.argtypes = [P, P, P, P, P, P, P, P, P]
+    L.or_assemble.argtypes = [I64, P, P, P, I64, P, P, P, I64, P, P, P, D, P, P, P, P, P, P]
+    L.or_recover.argtypes = [I64, P, P, P, P, P, P, D, P, P, P, P]
+    L.or_element_blocks.argtypes = [I64, P, P, P, P, P, D, P, P, P, P, P]
+    L.or_tet_recover.argtypes = [P, D, D, P, P, P, P, P, P]
+    for f in ("or_faces", "or_multipliers", "or_csr_pattern", "or_face_centroids", "or_tet_local",
+              "or_tet_matrices", "or_assemble", "or_recover", "or_element_blocks", "or_tet_recover"):
+        getattr(L, f).restype = ctypes.c_int
+    return L
+
+
 def _lib():
     global _LIB
     with _LOCK:
         if _LIB is None:
             build()
-            L = ctypes.CDLL(_SO)
-            P = ctypes.c_void_p
-            I64 = ctypes.c_int64
-            D = ctypes.c_double
-            L.or_faces.argtypes = [I64, I64, P, I64, P, P, P, P, P, P]
-            L.or_multipliers.argtypes = [I64, P, P, P]
-            L.or_csr_pattern.argtypes = [I64, P, P, I64, P, P, P]
-            L.or_face_centroids.argtypes = [I64, P, P, P]
-            L.or_tet_local.argtypes = [P, D, D, P, P, P, P, P, P]
-            L.or_tet_matrices.argtypes = [P, P, P, P, P, P, P, P, P]
-            L.or_assemble.argtypes = [I64, P, P, P, I64, P, P, P, I64, P, P, P, D, P, P, P, P, P, P]
-            L.or_recover.argtypes = [I64, P, P, P, P, P, P, D, P, P, P, P]
-            L.or_element_blocks.argtypes = [I64, P, P, P, P, P, D, P, P, P, P, P]
-            L.or_tet_recover.argtypes = [P, D, D, P, P, P, P, P, P]
-            for f in ("or_faces", "or_multipliers", "or_csr_pattern", "or_face_centroids", "or_tet_local",
-                      "or_tet_matrices", "or_assemble", "or_recover", "or_element_blocks", "or_tet_recover"):
-                getattr(L, f).restype = ctypes.c_int
-            _LIB = L
+            _LIB = _configure(ctypes.CDLL(_SO))
     return _LIB
+
+
+class use_library:
+    """Context manager: run the oracle functions on another build of
+    ph_oracle.c (the mutation tests load deliberately broken copies)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _LIB
+        _lib()
+        self.saved = _LIB
+        _LIB = _configure(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _LIB
+        _LIB = self.saved
+        return False
 
 
 def _p(a):
