@@ -259,6 +259,28 @@ ph_status ph_batch_get_config(const ph_batch* batch, int32_t* tile, int32_t* thr
 ph_status ph_batch_graph_launch(ph_batch* batch, void* stream);
 
 /*
+ * Uniform refinement on the device (Section 3.4, Listing RedRefine): every
+ * tet splits into 12 (4 at the vertices, 8 joining the faces of the inner
+ * octahedron to the centroid), with the edge numbering of Listing NumEdges
+ * and the listing's node numbering; boundary triples (the paper's Db, Nb)
+ * split 1 -> 4 at edge midpoints (refineFaces).  The result is bit-identical
+ * to the listing's arithmetic ((P0+P1+P2+P3)/4 and (Pa+Pb)/2).
+ *   coord [nC*3], tet [nE*4] (16-byte aligned), lists [nl*3] or NULL.
+ * Synchronises `stream` once (to size the output).  Errors: PH_ERR_ARG for
+ * invalid tets, a misaligned tet pointer or a list triple whose edges are not
+ * edges of the mesh; PH_ERR_OVERFLOW past the int32 range.
+ * ph_refined_info: refined counts (nC' = nC + nE + nEd, nE' = 12 nE,
+ * nl' = 4 nl) and nEd of the input mesh.  ph_refined_copy: device copies
+ * (each output may be NULL).  ph_refined_destroy: free in stream order.
+ */
+typedef struct ph_refined ph_refined;
+ph_status ph_refine(const double* coord, int64_t nC, const int32_t* tet, int64_t nE, const int32_t* lists,
+                    int64_t nl, void* stream, ph_refined** out);
+ph_status ph_refined_info(const ph_refined* r, int64_t* nC, int64_t* nE, int64_t* nEd_parent, int64_t* nl);
+ph_status ph_refined_copy(const ph_refined* r, double* coord, int32_t* tet, int32_t* lists, void* stream);
+ph_status ph_refined_destroy(ph_refined* r, void* stream);
+
+/*
  * y = H x for a CSR matrix (rowptr [n+1], colind, values) and x [n], y [n]
  * (float64 device arrays).  One kernel, no synchronisation.
  */

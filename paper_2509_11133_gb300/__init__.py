@@ -32,7 +32,7 @@ EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces",
            "ph_launch_count", "ph_solve_pcg_noalloc", "ph_recover_factored", "ph_spmv", "ph_misfit",
            "ph_adjoint_rhs", "ph_adjoint_grad", "ph_batch_create", "ph_batch_destroy", "ph_batch_bind",
            "ph_batch_assemble", "ph_batch_autotune", "ph_batch_set_config", "ph_batch_get_config",
-           "ph_batch_graph_launch")
+           "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy")
 
 
 class PHError(RuntimeError):
@@ -86,6 +86,10 @@ def load(path: str | None = None):
         "ph_batch_set_config": [P, I32, I32, I32, P],
         "ph_batch_get_config": [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)],
         "ph_batch_graph_launch": [P, P],
+        "ph_refine": [P, I64, P, I64, P, I64, P, ctypes.POINTER(P)],
+        "ph_refined_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)],
+        "ph_refined_copy": [P, P, P, P, P],
+        "ph_refined_destroy": [P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -321,6 +325,29 @@ class Mesh:
 
 def ph_mesh_create(coord, tet, neumann=None, stream=None) -> Mesh:
     return Mesh(coord, tet, neumann, stream)
+
+
+def ph_refine(coord, tet, lists=None, stream=None):
+    """One level of the 1->12 refinement on the device.  Returns (coord, tet,
+    lists, nEd) as CUDA tensors (lists None if none were given) and the edge
+    count of the input mesh."""
+    L = load()
+    coord, tet = coord.contiguous(), tet.contiguous()
+    nl = 0 if lists is None else lists.shape[0]
+    h = ctypes.c_void_p()
+    _check(L.ph_refine(_ptr(coord), coord.shape[0], _ptr(tet), tet.shape[0],
+                       _ptr(lists.contiguous()) if nl else None, nl, _stream(stream), ctypes.byref(h)), "ph_refine")
+    try:
+        nC, nE, nEd, nl2 = (ctypes.c_int64() for _ in range(4))
+        _check(L.ph_refined_info(h, ctypes.byref(nC), ctypes.byref(nE), ctypes.byref(nEd), ctypes.byref(nl2)),
+               "ph_refined_info")
+        c2 = torch.empty((nC.value, 3), dtype=torch.float64, device=coord.device)
+        t2 = torch.empty((nE.value, 4), dtype=torch.int32, device=coord.device)
+        l2 = torch.empty((nl2.value, 3), dtype=torch.int32, device=coord.device) if nl else None
+        _check(L.ph_refined_copy(h, _ptr(c2), _ptr(t2), _ptr(l2), _stream(stream)), "ph_refined_copy")
+    finally:
+        L.ph_refined_destroy(h, _stream(stream))
+    return c2, t2, l2, nEd.value
 
 
 def _ptr_array(tensors):
