@@ -325,6 +325,14 @@ const char* ph_last_error_message(void);
 /* Number of kernels this library has launched in this process. */
 int64_t ph_launch_count(void);
 
+/*
+ * y[i] = 1/x[i] with the device reciprocal the element kernels use for
+ * 1/|det E| and 1/det M (a Newton iteration; within one ulp of the rounded
+ * quotient, and the IEEE quotient for x outside [2^-1020, 2^1021)).  Device
+ * arrays of n doubles; exposed so that its accuracy can be tested.
+ */
+ph_status ph_rcp(const double* x, int64_t n, double* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

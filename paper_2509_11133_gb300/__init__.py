@@ -32,7 +32,7 @@ EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces",
            "ph_launch_count", "ph_solve_pcg_noalloc", "ph_recover_factored", "ph_spmv", "ph_misfit",
            "ph_adjoint_rhs", "ph_adjoint_grad", "ph_batch_create", "ph_batch_destroy", "ph_batch_bind",
            "ph_batch_assemble", "ph_batch_autotune", "ph_batch_set_config", "ph_batch_get_config",
-           "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy")
+           "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy", "ph_rcp")
 
 
 class PHError(RuntimeError):
@@ -90,6 +90,7 @@ def load(path: str | None = None):
         "ph_refined_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)],
         "ph_refined_copy": [P, P, P, P, P],
         "ph_refined_destroy": [P, P],
+        "ph_rcp": [P, I64, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -325,6 +326,14 @@ class Mesh:
 
 def ph_mesh_create(coord, tet, neumann=None, stream=None) -> Mesh:
     return Mesh(coord, tet, neumann, stream)
+
+
+def ph_rcp(x, stream=None):
+    """1/x with the device reciprocal of the element kernels (for testing)."""
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    _check(load().ph_rcp(_ptr(x), x.numel(), _ptr(y), _stream(stream)), "ph_rcp")
+    return y
 
 
 def ph_refine(coord, tet, lists=None, stream=None):

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(128) k_recover(int64_t nE, const double* __res
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nE) return;
   const double at = __ldg(a + t);
-  if (!(at > 0.0) || !(at < INFINITY)) {
+  if (!ph::pos_finite(at)) {
     ph_flag(status, PH_ERR_ARG);
     return;
   }

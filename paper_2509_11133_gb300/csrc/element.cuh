@@ -42,7 +42,7 @@ __device__ __forceinline__ void face_kernel(const Geo& G, double a, double c20, 
   double A12 = fma(m01, m02, -m00 * m12);
   double A22 = fma(m00, m11, -m01 * m01);
   const double detM = fma(m00, A00, fma(m01, A01, m02 * A02));
-  const double s = sc6 * G.rdet / detM;  // sc * 6/|det E| / det M
+  const double s = (sc6 * G.rdet) * ph::rcp_newton(detM);  // sc * 6/|det E| / det M
   A00 *= s; A01 *= s; A02 *= s; A11 *= s; A12 *= s; A22 *= s;
   // Y = adj(M) G_e T0^-1 (symmetric): upper triangle
   const double y00 = fma(A00, G.t00, fma(A01, G.t10, A02 * G.t20));
@@ -56,16 +56,16 @@ __device__ __forceinline__ void face_kernel(const Geo& G, double a, double c20, 
   Q[ut(0, 0)] = y22;
   Q[ut(0, 1)] = y02;
   Q[ut(0, 2)] = y12;
-  Q[ut(0, 3)] = -c2;
+  Q[ut(0, 3)] = ph::negate(c2);
   Q[ut(1, 1)] = y00;
   Q[ut(1, 2)] = y01;
-  Q[ut(1, 3)] = -c0;
+  Q[ut(1, 3)] = ph::negate(c0);
   Q[ut(2, 2)] = y11;
-  Q[ut(2, 3)] = -c1;
+  Q[ut(2, 3)] = ph::negate(c1);
   Q[ut(3, 3)] = c0 + c1 + c2;
 }
 
-__device__ __forceinline__ double neg_if(double x, bool n) { return n ? -x : x; }
+using ph::neg_if;
 
 
 // Local matrices, condensation and scatter of element t (Section 4.2-4.3,
@@ -80,7 +80,7 @@ __device__ __forceinline__ void assemble_element(int64_t t, const double* __rest
                                                  double* __restrict__ values, double* __restrict__ rhs,
                                                  double* __restrict__ factor, unsigned* status) {
   const double at = __ldg(a + t);
-  if (!(at > 0.0) || !(at < INFINITY)) {
+  if (!ph::pos_finite(at)) {
     ph_flag(status, PH_ERR_ARG);
     return;
   }
@@ -133,7 +133,7 @@ __device__ __forceinline__ void assemble_element(int64_t t, const double* __rest
     double e = base;
 #pragma unroll
     for (int m = 0; m < 4; ++m) e = fma(Q[ut(k, m)], h[m], e);
-    double g = neg_if(-ar[k] * e, neg[k]);
+    double g = neg_if(ar[k] * e, !neg[k]);
     if (UD && bnd) g = fma(ar[k], __ldg(uD + F[k]), g);  // b_D = |F| u_D(Ct_F)
     const int pd = comp(tp, k);
     if (bnd) {

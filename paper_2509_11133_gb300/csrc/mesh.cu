@@ -220,8 +220,8 @@ __global__ void k_tet_geom(const double* __restrict__ coord, const int4* __restr
   const double e2x = p2[0] - p0[0], e2y = p2[1] - p0[1], e2z = p2[2] - p0[2];
   const double e3x = p3[0] - p0[0], e3y = p3[1] - p0[1], e3z = p3[2] - p0[2];
   const double det = e1x * (e2y * e3z - e2z * e3y) + e1y * (e2z * e3x - e2x * e3z) + e1z * (e2x * e3y - e2y * e3x);
-  const double adet = fabs(det);
-  if (!(adet > 0.0) || !(adet < INFINITY)) ph_flag(status, PH_ERR_DEGENERATE);
+  const double adet = ph::neg_if(det, __double2hiint(det) < 0);  // |det| on the sign bit
+  if (!ph::pos_finite(adet)) ph_flag(status, PH_ERR_DEGENERATE);
   const double g00 = e1x * e1x + e1y * e1y + e1z * e1z, g01 = e1x * e2x + e1y * e2y + e1z * e2z;
   const double g02 = e1x * e3x + e1y * e3y + e1z * e3z, g11 = e2x * e2x + e2y * e2y + e2z * e2z;
   const double g12 = e2x * e3x + e2y * e3y + e2z * e3z, g22 = e3x * e3x + e3y * e3y + e3z * e3z;
@@ -235,7 +235,7 @@ __global__ void k_tet_geom(const double* __restrict__ coord, const int4* __restr
   gg[5] = make_double2(g11 - r1, g12 - r1);
   gg[6] = make_double2(g02 - r2, g12 - r2);
   gg[7] = make_double2(g22 - r2, adet);
-  gg[8] = make_double2(1.0 / adet, 0.0);
+  gg[8] = make_double2(ph::rcp_newton(adet), 0.0);
 }
 
 // 6. face areas 1/2 |(P_z - P_x) x (P_y - P_x)| (one thread per face)

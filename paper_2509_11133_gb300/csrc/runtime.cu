@@ -194,3 +194,17 @@ extern "C" const char* ph_status_string(ph_status s) {
 extern "C" const char* ph_last_error_message(void) { return ph::t_msg; }
 
 extern "C" int64_t ph_launch_count(void) { return ph::g_launches.load(); }
+
+namespace {
+__global__ void k_rcp(const double* __restrict__ x, int64_t n, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = ph::rcp_newton(x[i]);
+}
+}  // namespace
+
+extern "C" ph_status ph_rcp(const double* x, int64_t n, double* y, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return PH_ERR_ARG;
+  if (n == 0) return PH_OK;
+  k_rcp<<<ph::grid_for(n), ph::kThreads, 0, (cudaStream_t)stream>>>(x, n, y);
+  return ph::cuda_status(ph::launched(), "k_rcp");
+}
