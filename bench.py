@@ -69,21 +69,35 @@ def measured_peaks():
         return {}
 
 
-def profile_traffic():
-    """DRAM bytes per k_assemble launch from the committed ncu summary, or None
-    when assemble.cu has changed since the counters were taken."""
-    prof = os.path.join(ROOT, "profiles", "k_assemble_lognormal_3m.txt")
-    src = os.path.join(ROOT, "paper_2509_11133_gb300", "csrc", "assemble.cu")
+# kernels timed with the library's CUDA events inside the timed region
+TIMED_KERNELS = ("k_assemble", "k_zero_diag", "k_recover_factored")
+# sources that k_assemble is compiled from
+ASSEMBLE_SOURCES = ("assemble.cu", "element.cuh", "ph_internal.cuh")
+
+
+def assemble_sources_sha256():
+    h = hashlib.sha256()
+    for name in ASSEMBLE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2509_11133_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profile_traffic(nE):
+    """DRAM bytes of one k_assemble launch over nE elements: the per-element
+    figure of the committed ncu capture (taken on a smaller mesh of the same
+    recipe; traffic grows in proportion to the elements) times nE.  None when
+    the kernel's sources changed after the counters were taken."""
+    prof = os.path.join(ROOT, "profiles", "k_assemble_lognormal_1m.txt")
     try:
         kv = {}
         for line in open(prof):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if kv.get("assemble_cu_sha256") != sha:
+        if kv.get("sources_sha256") != assemble_sources_sha256():
             return None
-        return float(kv["dram_bytes_per_launch"])
+        return float(kv["dram_bytes_per_tet"]) * nE
     except (OSError, KeyError, ValueError):
         return None
 
@@ -234,11 +248,19 @@ def gpu_arm(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clocks.start()
     n_launch0 = ph.ph_launch_count()
+    for name in TIMED_KERNELS:
+        ph.ph_kernel_time(name, reset=True)
+    ph.ph_timing_enable(True)      # CUDA events around each element-kernel launch, on its stream
     for i in range(args.steps):
         step(evs[i])
         flush.zero_()          # L2 flush between timed steps (outside the event pairs)
     torch.cuda.synchronize()
+    ph.ph_timing_enable(False)
     n_launch = ph.ph_launch_count() - n_launch0
+    kern = {}
+    for name in TIMED_KERNELS:
+        ms, n = ph.ph_kernel_time(name, reset=True)
+        kern[name] = ms / n if n else float("nan")
     barrier()
     clk = clocks.stop()
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
@@ -293,16 +315,17 @@ def gpu_arm(args, rank, world, local_rank):
     e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in ee])) if ee else float("nan")
 
     # max over ranks
-    ms_per_step, e2e_ms, asm_max = max_over_ranks([ms_per_step, e2e_ms, float(np.mean(asm_ms))], world, dev)
+    ms_per_step, e2e_ms, asm_max, k_asm = max_over_ranks(
+        [ms_per_step, e2e_ms, float(np.mean(asm_ms)), kern["k_assemble"]], world, dev)
 
     if rank != 0:
         return None
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
-    asm_s = asm_max * 1e-3
+    asm_s = k_asm * 1e-3          # one k_assemble launch, CUDA events on its stream
     ops = ASSEMBLE_OPS_PER_TET * nE
     achieved_gops = ops / asm_s / 1e9
-    traffic = profile_traffic()
+    traffic = profile_traffic(nE)
     bpt = assemble_bytes_per_tet(nE, p.nC, nF)
     value = whole_job_rate(nE, world, ms_per_step)
     line = {
@@ -330,8 +353,9 @@ def gpu_arm(args, rank, world, local_rank):
         },
         "phases_ms": {"mesh_create": float(np.mean(create_ms)), "assemble": float(np.mean(asm_ms)),
                       "recover": float(np.mean(rec_ms))},
+        "kernels_ms": kern,
         "roofline": {
-            "kernel": "k_assemble (timed as the ph_assemble call: k_zero_diag + k_assemble)",
+            "kernel": "k_assemble (average launch over the timed steps, CUDA events on its stream)",
             "bound": "alu",
             "achieved": achieved_gops,
             "peak": FP64_PEAK_GOPS,

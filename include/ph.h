@@ -78,22 +78,26 @@ typedef struct {
 /*
  * Build a mesh: connectivity, numbering, CSR pattern and element geometry.
  *   coord   [nC*3] float64, vertex coordinates.
- *   tet     [nE*4] int32, vertex ids of each tetrahedron (any orientation).
+ *   tet     [nE*4] int32, vertex ids of each tetrahedron (any orientation);
+ *           16-byte aligned (read as int4).
  *   neumann [nN*3] int32 vertex triples of the Neumann boundary faces (the
  *           paper's Nb, Listing 1), or NULL with nN = 0.  Every other boundary
  *           face is Dirichlet.
  * Connectivity follows Section 3.3 (FacesUp) and the jump convention of
  * Section 2.2; it is computed on the device by bucketing face keys by their
- * smallest vertex and matching within buckets, and is bit-identical to the
- * definition (first occurrence numbering).
- * Work already queued on `stream` is waited for, the build runs on two
- * internal streams (connectivity at high priority, element geometry at low
- * priority) and later work on `stream` is ordered after it.  The call blocks
- * the host until the mesh is built (it must read the face and CSR sizes).
+ * largest vertex (and two bits of the middle one) and matching within
+ * buckets, and is bit-identical to the definition (first occurrence
+ * numbering).
+ * Runs in order on `stream`.  Face and CSR arrays are sized by the bounds
+ * nF <= 4 nE + nN and nnz <= 16 nE + nN, so the build is enqueued at once and
+ * the call blocks the host once, at the end, to read the counts and the
+ * first error.
  * Errors: PH_ERR_ARG for ids out of [0, nC), repeated vertices in a tet, a
- * Neumann triple that is not a boundary face of the mesh or is listed twice;
- * PH_ERR_NONMANIFOLD; PH_ERR_DEGENERATE for det = 0; PH_ERR_OVERFLOW when
- * 4 nE + nN, nF or nnz reaches 2^31.  On error *out is NULL.
+ * Neumann triple that is not a boundary face of the mesh or is listed twice,
+ * a misaligned tet pointer; PH_ERR_NONMANIFOLD; PH_ERR_DEGENERATE for
+ * det = 0; PH_ERR_OVERFLOW when 16 nE + nN or nC reaches 2^31 - 1; a
+ * look-back wait of a scan that timed out gives PH_ERR_TIMEOUT.  On error
+ * *out is NULL.
  * Release with ph_mesh_destroy.
  */
 ph_status ph_mesh_create(const double* coord, int64_t nC, const int32_t* tet, int64_t nE,
@@ -324,6 +328,18 @@ const char* ph_last_error_message(void);
 
 /* Number of kernels this library has launched in this process. */
 int64_t ph_launch_count(void);
+
+/*
+ * Kernel timing, off by default.  While enabled, the library records a pair
+ * of CUDA events around each launch of k_assemble, k_zero_diag, k_recover and
+ * k_recover_factored on the stream it launches on (not while that stream is
+ * being captured into a graph).  ph_kernel_time waits for the recorded events
+ * of the named kernel, adds their elapsed times to its running total and
+ * returns the total device time in ms and the number of launches timed;
+ * reset != 0 clears the total afterwards.  An unknown name returns 0, 0.
+ */
+ph_status ph_timing_enable(int on);
+ph_status ph_kernel_time(const char* kernel, int reset, double* ms, int64_t* launches);
 
 /*
  * y[i] = 1/x[i] with the device reciprocal the element kernels use for

@@ -32,7 +32,8 @@ EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces",
            "ph_launch_count", "ph_solve_pcg_noalloc", "ph_recover_factored", "ph_spmv", "ph_misfit",
            "ph_adjoint_rhs", "ph_adjoint_grad", "ph_batch_create", "ph_batch_destroy", "ph_batch_bind",
            "ph_batch_assemble", "ph_batch_autotune", "ph_batch_set_config", "ph_batch_get_config",
-           "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy", "ph_rcp")
+           "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy", "ph_rcp", "ph_timing_enable",
+           "ph_kernel_time")
 
 
 class PHError(RuntimeError):
@@ -91,6 +92,8 @@ def load(path: str | None = None):
         "ph_refined_copy": [P, P, P, P, P],
         "ph_refined_destroy": [P, P],
         "ph_rcp": [P, I64, P, P],
+        "ph_timing_enable": [ctypes.c_int],
+        "ph_kernel_time": [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(D), ctypes.POINTER(I64)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -326,6 +329,19 @@ class Mesh:
 
 def ph_mesh_create(coord, tet, neumann=None, stream=None) -> Mesh:
     return Mesh(coord, tet, neumann, stream)
+
+
+def ph_timing_enable(on: bool = True):
+    """Switch the library's per-kernel CUDA-event timing on or off."""
+    _check(load().ph_timing_enable(1 if on else 0), "ph_timing_enable")
+
+
+def ph_kernel_time(kernel: str, reset: bool = False):
+    """(total device ms, launches) of the named kernel while timing was on."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(load().ph_kernel_time(kernel.encode(), 1 if reset else 0, ctypes.byref(ms), ctypes.byref(n)),
+           "ph_kernel_time")
+    return ms.value, n.value
 
 
 def ph_rcp(x, stream=None):

@@ -164,8 +164,10 @@ extern "C" ph_status ph_assemble(const ph_mesh* m, const double* a, double c, co
   if ((m->nnz > 0 && !values) || (m->L > 0 && !rhs)) return PH_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (m->L > 0) {
+    KernelTimer kt("k_zero_diag", s);
     k_zero_diag<<<grid_for(m->L), kThreads, 0, s>>>(m->L, m->rowdiag, values, rhs);
     cudaError_t e = launched();
+    kt.stop();
     if (e != cudaSuccess) return cuda_status(e, "k_zero_diag");
   }
   if (m->nE == 0) return PH_OK;
@@ -176,6 +178,7 @@ extern "C" ph_status ph_assemble(const ph_mesh* m, const double* a, double c, co
                                                   m->face_area, a, c20, six_over_c, f_face, uD_face, gN_face, \
                                                   values, rhs, factor, m->status)
   const bool ud = uD_face != nullptr && m->nFd > 0, gn = gN_face != nullptr && m->nFn > 0;
+  KernelTimer kt("k_assemble", s);
   if (factor) {
     if (ud && gn) PH_ASM(true, true, true);
     else if (ud) PH_ASM(true, false, true);
@@ -188,7 +191,9 @@ extern "C" ph_status ph_assemble(const ph_mesh* m, const double* a, double c, co
     else PH_ASM(false, false, false);
   }
 #undef PH_ASM
-  return cuda_status(launched(), "k_assemble");
+  const cudaError_t e = launched();
+  kt.stop();
+  return cuda_status(e, "k_assemble");
 }
 
 extern "C" ph_status ph_recover(const ph_mesh* m, const double* a, double c, const double* f_face,
@@ -199,13 +204,16 @@ extern "C" ph_status ph_recover(const ph_mesh* m, const double* a, double c, con
   cudaStream_t s = (cudaStream_t)stream;
   const double c20 = c / 20.0, six_over_c = 6.0 / c;
   const unsigned grid = grid_for(m->nE, 128);
+  KernelTimer kt("k_recover", s);
   if (gN_face != nullptr && m->nFn > 0)
     k_recover<true><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->face_area, a, c20, six_over_c, f_face,
                                          gN_face, lambda, u, m->status);
   else
     k_recover<false><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->face_area, a, c20, six_over_c,
                                           f_face, gN_face, lambda, u, m->status);
-  return cuda_status(launched(), "k_recover");
+  const cudaError_t e = launched();
+  kt.stop();
+  return cuda_status(e, "k_recover");
 }
 
 extern "C" ph_status ph_recover_factored(const ph_mesh* m, const double* factor, double c, const double* f_face,
@@ -216,11 +224,14 @@ extern "C" ph_status ph_recover_factored(const ph_mesh* m, const double* factor,
   cudaStream_t s = (cudaStream_t)stream;
   const double six_over_c = 6.0 / c;
   const unsigned grid = grid_for(m->nE, 128);
+  KernelTimer kt("k_recover_factored", s);
   if (gN_face != nullptr && m->nFn > 0)
     k_recover_factored<true><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->face_area, factor,
                                                   six_over_c, f_face, gN_face, lambda, u);
   else
     k_recover_factored<false><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->face_area, factor,
                                                    six_over_c, f_face, gN_face, lambda, u);
-  return cuda_status(launched(), "k_recover_factored");
+  const cudaError_t e = launched();
+  kt.stop();
+  return cuda_status(e, "k_recover_factored");
 }

@@ -48,6 +48,19 @@ inline cudaError_t launched(int n = 1) {
   return cudaGetLastError();
 }
 
+// Opt-in device timing of named kernels (ph_timing_enable): brackets one
+// launch with CUDA events on its stream; a no-op while timing is off or the
+// stream is being captured into a graph.
+class KernelTimer {
+ public:
+  KernelTimer(const char* name, cudaStream_t s);
+  void stop();  // after the launch
+ private:
+  const char* name_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
 void set_error_message(const char* what, cudaError_t e);
 void set_error_text(const char* text);
 ph_status cuda_status(cudaError_t e, const char* what);
@@ -60,9 +73,13 @@ inline cudaError_t alloc(T** p, size_t n, cudaStream_t s) {
 }
 void free_async(void* p, cudaStream_t s);
 
-// Exclusive prefix sum of n int32 values into out (int32); the int64 total
-// is written to *d_total (device).  in and out may alias.
-ph_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* d_total, cudaStream_t s);
+// Exclusive prefix sum of n non-negative int32 values into out (int32), one
+// kernel; the int64 total is written to *d_total (device).  in and out may
+// alias.  With d_len, only min(n, *d_len + len_add) values (a length known
+// on the device) are scanned.  A look-back wait that times out sets
+// PH_ERR_TIMEOUT in *status (if given) instead of hanging.
+ph_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* d_total, cudaStream_t s,
+                         unsigned* status = nullptr, const int64_t* d_len = nullptr, int64_t len_add = 0);
 
 // First error recorded in a status word (lowest code), PH_OK if none.
 inline ph_status status_from_bits(unsigned bits) {

@@ -234,7 +234,7 @@ extern "C" ph_status ph_refine(const double* coord, int64_t nC, const int32_t* t
     k_edge_count<<<grid_for(nE), kThreads, 0, s>>>(reinterpret_cast<const int4*>(tet), nE, nC, cnt, status);
     RF_CU(launched());
   }
-  st = exclusive_scan(cnt, start, nC + 1, d_tot, s);
+  st = exclusive_scan(cnt, start, nC + 1, d_tot, s, status);
   if (st != PH_OK) goto fail;
   if (nE > 0) {
     k_edge_fill<<<grid_for(nE), kThreads, 0, s>>>(reinterpret_cast<const int4*>(tet), nE, nC, start, cnt, entries,
@@ -245,7 +245,7 @@ extern "C" ph_status ph_refine(const double* coord, int64_t nC, const int32_t* t
     RF_CU(launched(3));
   }
   RF_CU(cudaMemsetAsync(ebase + nE, 0, sizeof(int32_t), s));
-  st = exclusive_scan(ebase, ebase, nE + 1, d_tot, s);
+  st = exclusive_scan(ebase, ebase, nE + 1, d_tot, s, status);
   if (st != PH_OK) goto fail;
   RF_CU(cudaMemcpyAsync(&tot, d_tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   RF_CU(cudaMemcpyAsync(&bits, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));

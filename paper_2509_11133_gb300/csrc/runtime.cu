@@ -3,7 +3,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
+#include <string>
+#include <vector>
 
 #include "ph_internal.cuh"
 
@@ -107,70 +110,114 @@ __device__ __forceinline__ T block_excl_scan(T v, T* total) {
   return before;
 }
 
-__global__ void k_scan_reduce(const int32_t* __restrict__ in, int64_t n, int64_t* __restrict__ tile_sums) {
-  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-  int64_t s = 0;
-#pragma unroll
-  for (int i = 0; i < SCAN_I; ++i) {
-    int64_t idx = base + (int64_t)i * SCAN_T + threadIdx.x;
-    if (idx < n) s += in[idx];
-  }
-  int64_t tot;
-  block_excl_scan<int64_t, SCAN_T>(s, &tot);
-  if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
-}
+// Single-pass exclusive scan with decoupled look-back (Merrill and Garland,
+// "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016).  Tiles
+// of SCAN_TILE elements take ids from an atomic counter in the order the
+// blocks start, so every predecessor of a tile is running or done.  A tile
+// publishes its aggregate (flag 1); its first warp then reads the state of
+// 32 predecessors at a time, adds the values up to the nearest one that
+// carries an inclusive prefix (flag 2), and the tile publishes its own
+// inclusive prefix.  State word: flag in bits 62..63, value in bits 0..61
+// (inputs are non-negative counts).
+constexpr unsigned long long kScanAgg = 1ull << 62, kScanInc = 2ull << 62, kScanVal = (1ull << 62) - 1;
+constexpr int kScanSpinLimit = 1 << 20;  // unready polls before giving up (>= 32 ns apart)
 
-// One block: exclusive scan of the tile sums in place; total to *d_total.
-__global__ void k_scan_tiles(int64_t* __restrict__ tile_sums, int64_t ntiles, int64_t* __restrict__ d_total) {
-  int64_t carry = 0;
-  for (int64_t base = 0; base < ntiles; base += 1024) {
-    int64_t idx = base + threadIdx.x;
-    int64_t v = idx < ntiles ? tile_sums[idx] : 0;
-    int64_t tot;
-    int64_t ex = block_excl_scan<int64_t, 1024>(v, &tot);
-    if (idx < ntiles) tile_sums[idx] = carry + ex;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) *d_total = carry;
-}
-
-__global__ void k_scan_apply(const int32_t* in, int32_t* out, int64_t n, const int64_t* __restrict__ tile_offs) {
-  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_I;
+__global__ void __launch_bounds__(SCAN_T) k_scan(const int32_t* in, int32_t* out, int64_t nmax,
+                                                  const int64_t* __restrict__ d_len, int64_t len_add,
+                                                  int64_t* __restrict__ d_total, unsigned long long* state,
+                                                  unsigned* counter, unsigned* status) {
+  __shared__ unsigned s_tile;
+  __shared__ int64_t s_prefix;
+  if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+  __syncthreads();
+  const int64_t n = d_len ? min(nmax, *d_len + len_add) : nmax;
+  const int64_t tile = s_tile;
+  const int64_t last = n > 0 ? (n - 1) / SCAN_TILE : 0;
+  if (tile > last) return;  // past the device-side length: nobody looks back at it
+  const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_I;
+  const bool vec = base + SCAN_I <= n && ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   int32_t v[SCAN_I];
-  int64_t s = 0;
+  if (vec) {
+    const int4 a = *reinterpret_cast<const int4*>(in + base), b = *reinterpret_cast<const int4*>(in + base + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
 #pragma unroll
-  for (int i = 0; i < SCAN_I; ++i) {
-    int64_t idx = base + i;
-    v[i] = idx < n ? in[idx] : 0;
-    s += v[i];
+    for (int i = 0; i < SCAN_I; ++i) v[i] = base + i < n ? in[base + i] : 0;
   }
+  int64_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_I; ++i) sum += v[i];
   int64_t tot;
-  int64_t run = tile_offs[blockIdx.x] + block_excl_scan<int64_t, SCAN_T>(s, &tot);
+  const int64_t ex = block_excl_scan<int64_t, SCAN_T>(sum, &tot);
+  if (threadIdx.x < 32) {
+    volatile unsigned long long* st = state;
+    const int lane = threadIdx.x;
+    int64_t prefix = 0;
+    if (tile > 0) {
+      if (lane == 0) st[tile] = kScanAgg | (unsigned long long)tot;
+      int spins = 0;
+      for (int64_t p = tile - 1; p >= 0;) {
+        const int64_t q = p - lane;  // lane 0 is the nearest predecessor
+        unsigned long long w = kScanInc;  // before tile 0: an inclusive prefix of 0
+        if (q >= 0) w = st[q];
+        while (__any_sync(0xFFFFFFFFu, (w >> 62) == 0)) {
+          if (++spins > kScanSpinLimit) break;
+          __nanosleep(32);
+          if ((w >> 62) == 0) w = st[q];
+        }
+        if (spins > kScanSpinLimit) {  // a predecessor never published: give up, flagged
+          if (lane == 0 && status) ph_flag(status, PH_ERR_TIMEOUT);
+          break;
+        }
+        const unsigned inc = __ballot_sync(0xFFFFFFFFu, (w >> 62) == 2);
+        const int stop = inc ? __ffs(inc) - 1 : 31;  // add lanes 0..stop
+        int64_t x = lane <= stop ? (int64_t)(w & kScanVal) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+        prefix += __shfl_sync(0xFFFFFFFFu, x, 0);
+        if (inc) break;
+        p -= 32;
+      }
+    }
+    if (lane == 0) {
+      __threadfence();
+      st[tile] = kScanInc | (unsigned long long)(prefix + tot);
+      s_prefix = prefix;
+      if (tile == last && d_total) *d_total = prefix + tot;
+    }
+  }
+  __syncthreads();
+  int64_t run = s_prefix + ex;
+  int32_t o[SCAN_I];
 #pragma unroll
   for (int i = 0; i < SCAN_I; ++i) {
-    int64_t idx = base + i;
-    if (idx < n) out[idx] = (int32_t)run;
+    o[i] = (int32_t)run;
     run += v[i];
   }
+  if (vec) {
+    *reinterpret_cast<int4*>(out + base) = make_int4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<int4*>(out + base + 4) = make_int4(o[4], o[5], o[6], o[7]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < SCAN_I; ++i)
+      if (base + i < n) out[base + i] = o[i];
+  }
 }
 
-ph_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* d_total, cudaStream_t s) {
+ph_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* d_total, cudaStream_t s,
+                         unsigned* status, const int64_t* d_len, int64_t len_add) {
   int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (ntiles < 1) ntiles = 1;
-  int64_t* tiles = nullptr;
-  cudaError_t e = alloc(&tiles, (size_t)ntiles, s);
+  unsigned long long* state = nullptr;  // ntiles words, then the tile counter
+  cudaError_t e = alloc(&state, (size_t)ntiles + 1, s);
   if (e != cudaSuccess) return cuda_status(e, "scan alloc");
-  k_scan_reduce<<<(unsigned)ntiles, SCAN_T, 0, s>>>(in, n, tiles);
-  e = launched();
+  e = cudaMemsetAsync(state, 0, sizeof(unsigned long long) * (ntiles + 1), s);
   if (e == cudaSuccess) {
-    k_scan_tiles<<<1, 1024, 0, s>>>(tiles, ntiles, d_total);
+    k_scan<<<(unsigned)ntiles, SCAN_T, 0, s>>>(in, out, n, d_len, len_add, d_total, state,
+                                               reinterpret_cast<unsigned*>(state + ntiles), status);
     e = launched();
   }
-  if (e == cudaSuccess) {
-    k_scan_apply<<<(unsigned)ntiles, SCAN_T, 0, s>>>(in, out, n, tiles);
-    e = launched();
-  }
-  free_async(tiles, s);
+  free_async(state, s);
   return cuda_status(e, "scan");
 }
 
@@ -194,6 +241,80 @@ extern "C" const char* ph_status_string(ph_status s) {
 extern "C" const char* ph_last_error_message(void) { return ph::t_msg; }
 
 extern "C" int64_t ph_launch_count(void) { return ph::g_launches.load(); }
+
+// --- kernel timing ---------------------------------------------------------
+namespace ph {
+namespace {
+struct TimedLaunch {
+  const char* name;
+  cudaEvent_t a, b;
+};
+std::atomic<bool> g_timing{false};
+std::mutex g_timing_mu;
+std::vector<TimedLaunch> g_timed;                          // recorded, not yet read
+std::map<std::string, std::pair<double, int64_t>> g_time;  // name -> (ms, launches)
+}  // namespace
+
+KernelTimer::KernelTimer(const char* name, cudaStream_t s) : name_(name), s_(s) {
+  if (!g_timing.load(std::memory_order_relaxed)) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+  if (cudaEventCreate(&a_) != cudaSuccess) { a_ = nullptr; return; }
+  if (cudaEventCreate(&b_) != cudaSuccess || cudaEventRecord(a_, s) != cudaSuccess) {
+    cudaEventDestroy(a_);
+    if (b_) cudaEventDestroy(b_);
+    a_ = b_ = nullptr;
+  }
+}
+
+void KernelTimer::stop() {
+  if (!a_) return;
+  if (cudaEventRecord(b_, s_) != cudaSuccess) {
+    cudaEventDestroy(a_);
+    cudaEventDestroy(b_);
+  } else {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_timed.push_back({name_, a_, b_});
+  }
+  a_ = b_ = nullptr;
+}
+}  // namespace ph
+
+extern "C" ph_status ph_timing_enable(int on) {
+  ph::g_timing.store(on != 0);
+  return PH_OK;
+}
+
+extern "C" ph_status ph_kernel_time(const char* kernel, int reset, double* ms, int64_t* launches) {
+  if (!kernel) return PH_ERR_ARG;
+  std::lock_guard<std::mutex> lk(ph::g_timing_mu);
+  cudaError_t err = cudaSuccess;
+  std::vector<ph::TimedLaunch> keep;
+  for (const ph::TimedLaunch& t : ph::g_timed) {
+    if (strcmp(t.name, kernel) != 0) {
+      keep.push_back(t);
+      continue;
+    }
+    float f = 0.f;
+    cudaError_t e = cudaEventSynchronize(t.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&f, t.a, t.b);
+    if (e == cudaSuccess) {
+      auto& acc = ph::g_time[kernel];
+      acc.first += f;
+      acc.second += 1;
+    } else if (err == cudaSuccess) {
+      err = e;
+    }
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  ph::g_timed.swap(keep);
+  auto it = ph::g_time.find(kernel);
+  if (ms) *ms = it == ph::g_time.end() ? 0.0 : it->second.first;
+  if (launches) *launches = it == ph::g_time.end() ? 0 : it->second.second;
+  if (reset && it != ph::g_time.end()) ph::g_time.erase(it);
+  return ph::cuda_status(err, "ph_kernel_time");
+}
 
 namespace {
 __global__ void k_rcp(const double* __restrict__ x, int64_t n, double* __restrict__ y) {

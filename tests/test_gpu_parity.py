@@ -111,7 +111,18 @@ def assert_values_close(g, o):
 
 
 CASES = ["listing1", "listing1_mixed", "sin_kuhn", "kuhn_m2_k1", "shuffled", "mixed_l2", "lognormal_small",
-         "jitter_checker_small"]
+         "jitter_checker_small", "degree_sorted", "mixed_degree_sorted"]
+
+
+def renumber_by_degree(coord, tet, lists=()):
+    """Vertices renumbered by ascending number of incident tets, so that the
+    busiest vertices are the largest ids of most of their faces: face-key
+    buckets of up to 108 entries (tet and Neumann keys mixed)."""
+    deg = np.bincount(tet.ravel(), minlength=coord.shape[0])
+    order = np.argsort(deg, kind="stable")
+    inv = np.empty_like(order)
+    inv[order] = np.arange(order.size)
+    return coord[order], inv[tet].astype(np.int32), [inv[l].astype(np.int32) for l in lists]
 
 
 def make_case(name):
@@ -130,6 +141,15 @@ def make_case(name):
         return meshgen.Problem(name, coord, tet, meshgen.lognormal_field(tet.shape[0], 9), 0.3, p.f)
     if name == "mixed_l2":
         return meshgen.problem("paper_mixed", 2)
+    if name == "degree_sorted":
+        p = meshgen.problem("kuhn_m2_k1")
+        coord, tet, _ = renumber_by_degree(p.coord, p.tet)
+        return meshgen.Problem(name, coord, tet, meshgen.lognormal_field(tet.shape[0], 3), 0.5, p.f)
+    if name == "mixed_degree_sorted":
+        p = meshgen.problem("paper_mixed", 2)
+        coord, tet, (neu,) = renumber_by_degree(p.coord, p.tet, [p.neumann])
+        p.coord, p.tet, p.neumann = coord, tet, neu
+        return p
     if name == "lognormal_small":
         # the lognormal workload's recipe on a 3^3 cube refined twice (23,328 tets:
         # many blocks and a ragged tail)
