@@ -99,10 +99,12 @@ __device__ __forceinline__ void tet_geom(const double* __restrict__ coord, int4 
 
 // 1. histogram of face keys by bucket
 __global__ void k_face_count(const int4* __restrict__ tet, int64_t nE, int64_t nC, const int32_t* __restrict__ nb,
-                             int64_t nN, int sub, int32_t* __restrict__ cnt, unsigned* status) {
+                             int64_t nN, int sub, int32_t* __restrict__ cnt, int4* __restrict__ tet_copy,
+                             unsigned* status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < nE) {
     int4 v = tet[i];
+    tet_copy[i] = v;  // the mesh's own copy of the input
     if (!valid_tet(v, nC)) { ph_flag(status, PH_ERR_ARG); return; }
 #pragma unroll
     for (int k = 0; k < 4; ++k) atomicAdd(&cnt[bucket_of(sort3(local_face(v, k)), sub)], 1);
@@ -219,11 +221,15 @@ __device__ __forceinline__ int first_rank(int4 m, int s0, int k) {
 }
 
 // 5. per tet: face ids, T+/T-, T+'s tuple, kind and non-Neumann flag of the
-//    faces it owns (first occurrences).
+//    faces it owns (first occurrences).  Without Neumann faces (mult_iota
+//    given) every face has a multiplier, l(F) = F, so the tet also writes its
+//    slots' multiplier ids and, for the faces it owns, the row length 1 + 3
+//    per tet of the face (7 interior, 4 boundary); k_tet_mult is not needed.
 __global__ void k_face_emit(const int4* __restrict__ tet, int64_t nE, const int4* __restrict__ mate4,
                             const int32_t* __restrict__ fbase, int4* __restrict__ tface, int2* __restrict__ face_tet,
                             int32_t* __restrict__ face_vtx, int8_t* __restrict__ face_kind,
-                            int32_t* __restrict__ flag, int32_t* __restrict__ mult_iota, const unsigned* status) {
+                            int32_t* __restrict__ flag, int32_t* __restrict__ mult_iota, int4* __restrict__ tmult,
+                            int32_t* __restrict__ rowlen, const unsigned* status) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nE || failed(status)) return;
   int4 v = tet[t];
@@ -244,7 +250,11 @@ __global__ void k_face_emit(const int4* __restrict__ tet, int64_t nE, const int4
       const int kind = mk >= 0 ? 0 : (mk == -1 ? 1 : 2);
       face_kind[F] = (int8_t)kind;
       if (flag) flag[F] = kind != 2;      // Neumann faces present: multipliers by a scan of the flags
-      if (mult_iota) mult_iota[F] = F;    // none: l(F) = F
+      if (mult_iota) {                    // none: l(F) = F
+        mult_iota[F] = F;
+        rowlen[F] = mk >= 0 ? 7 : 4;
+        if (F + 1 == fbase[nE]) rowlen[F + 1] = 0;  // the scan reads one entry past the last row
+      }
     } else {
       int t2 = mk >> 2, k2 = mk & 3;
       int F = fbase[t2] + first_rank(mate4[t2], 4 * t2, k2);
@@ -252,6 +262,12 @@ __global__ void k_face_emit(const int4* __restrict__ tet, int64_t nE, const int4
     }
   }
   tface[t] = make_int4(out[0], out[1], out[2], out[3]);
+  if (mult_iota) {
+    int o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[k] = (int)((unsigned)(out[k] & PH_ID_MASK) | (comp(m, k) < 0 ? PH_BND_BIT : 0u));
+    tmult[t] = make_int4(o[0], o[1], o[2], o[3]);
+  }
 }
 
 // face area 1/2 |(P_z - P_x) x (P_y - P_x)|
@@ -471,7 +487,6 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   PH_CU(alloc(&m->tet, (size_t)nE, s), "alloc tet");
   PH_CU(alloc(&m->geo, (size_t)(PH_GEO_STRIDE * nE), s), "alloc");
   if (nC > 0) PH_CU(cudaMemcpyAsync(m->coord, coord, sizeof(double) * 3 * nC, cudaMemcpyDeviceToDevice, s), "copy");
-  if (nE > 0) PH_CU(cudaMemcpyAsync(m->tet, tet, sizeof(int4) * nE, cudaMemcpyDeviceToDevice, s), "copy");
 
   // --- faces: bucket the keys, match them, number the faces ----------------
   PH_CU(alloc(&cnt, (size_t)nb, s), "alloc");
@@ -482,7 +497,8 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   PH_CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)nb, s), "memset");
   PH_CU(cudaMemsetAsync(newc, 0, sizeof(int32_t) * (nE + 1), s), "memset");
   if (nent > 0) {
-    k_face_count<<<grid_for(nE + nN), kThreads, 0, s>>>(m->tet, nE, nC, neumann, nN, sub, cnt, m->status);
+    k_face_count<<<grid_for(nE + nN), kThreads, 0, s>>>(reinterpret_cast<const int4*>(tet), nE, nC, neumann, nN,
+                                                        sub, cnt, m->tet, m->status);
     PH_CU(launched(), "k_face_count");
   }
   PH_TRY(exclusive_scan(cnt, start, nb, d_tot, s, m->status));
@@ -508,6 +524,9 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   PH_CU(alloc(&m->face_kind, (size_t)nFmax, s), "alloc");
   PH_CU(alloc(&m->face_mult, (size_t)nFmax + 1, s), "alloc");
   PH_CU(alloc(&m->face_area, (size_t)nFmax, s), "alloc");
+  PH_CU(alloc(&m->tmult, (size_t)nE, s), "alloc");
+  PH_CU(alloc(&rowlen, (size_t)nFmax + 1, s), "alloc");
+  PH_CU(alloc(&m->rowptr, (size_t)nFmax + 1, s), "alloc");
   if (nN > 0) {
     PH_CU(alloc(&flag, (size_t)nFmax + 1, s), "alloc");
     PH_CU(cudaMemsetAsync(flag, 0, sizeof(int32_t) * (nFmax + 1), s), "memset");
@@ -515,7 +534,7 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   if (nE > 0) {
     k_face_emit<<<grid_for(nE), kThreads, 0, s>>>(m->tet, nE, reinterpret_cast<int4*>(mate), newc, m->tface,
                                                   m->face_tet, m->face_vtx, m->face_kind, flag,
-                                                  nN > 0 ? nullptr : m->face_mult, m->status);
+                                                  nN > 0 ? nullptr : m->face_mult, m->tmult, rowlen, m->status);
     PH_CU(launched(), "k_face_emit");
   }
   free_async(mate, s); mate = nullptr;
@@ -530,11 +549,9 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   } else {  // every face has a multiplier (written by k_face_emit): L = nF
     PH_CU(cudaMemcpyAsync(d_tot + 1, d_tot, sizeof(int64_t), cudaMemcpyDeviceToDevice, s), "copy");
   }
-  PH_CU(alloc(&m->tmult, (size_t)nE, s), "alloc");
-  PH_CU(alloc(&rowlen, (size_t)nFmax + 1, s), "alloc");
-  PH_CU(alloc(&m->rowptr, (size_t)nFmax + 1, s), "alloc");
-  PH_CU(cudaMemsetAsync(rowlen, 0, sizeof(int32_t) * (nFmax + 1), s), "memset");
-  if (nE > 0) {
+  // without Neumann faces k_face_emit wrote tmult and the row lengths
+  if (nN > 0 || nE == 0) PH_CU(cudaMemsetAsync(rowlen, 0, sizeof(int32_t) * (nFmax + 1), s), "memset");
+  if (nN > 0 && nE > 0) {
     k_tet_mult<<<grid_for(nE), kThreads, 0, s>>>(m->tface, nE, m->face_mult, m->face_tet, m->tmult, rowlen,
                                                  m->status);
     PH_CU(launched(), "k_tet_mult");

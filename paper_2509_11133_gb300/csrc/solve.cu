@@ -12,13 +12,17 @@ constexpr int RT = 256;   // threads per block
 constexpr int RB = 1216;  // blocks (8 x 152 SMs) for vector kernels and partial sums
 
 struct Scalars {
-  double rz, pq, alpha, beta, rr, bb, rz_next;
+  double rz, pq, alpha, beta, rr, bb;
+  unsigned done;  // blocks finished in the current reducing kernel (last-block detection)
+  unsigned bad;   // a non-positive diagonal entry was seen
 };
 
-// Workspace of one solve (doubles): r, p, q, dinv (4 n), then the partial sums
-// part[0, RB) = p.q, part[RB, 2RB) = r.z, part[2RB, 3RB) = r.r, then Scalars
-// and a flag word.
+// Workspace of one solve (doubles): r, p, q, dinv (4 vectors of vec_stride(n)
+// doubles, so each starts 256-byte aligned), then the partial sums
+// part[0, RB) = p.q, part[RB, 2RB) = r.z, part[2RB, 3RB) = r.r, then Scalars.
 constexpr size_t kPart = 3 * (size_t)RB;
+inline size_t vec_stride(int64_t n) { return ((size_t)n + 31) & ~(size_t)31; }
+inline size_t workspace_doubles(int64_t n) { return 4 * vec_stride(n) + kPart + (sizeof(Scalars) + 7) / 8; }
 
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double sm[RT / 32];
@@ -34,11 +38,25 @@ __device__ __forceinline__ double block_sum(double v) {
   return r;  // valid in thread 0
 }
 
-// Sum of part[off, off + RB) in a fixed order (every caller gets the same value).
+// Sum of part[off, off + RB) in a fixed order (every caller gets the same
+// value); the partials come from other blocks, so they bypass L1.
 __device__ __forceinline__ double sum_partials(const double* __restrict__ part, int off) {
   double v = 0.0;
-  for (int i = threadIdx.x; i < RB; i += RT) v += part[off + i];
+  for (int i = threadIdx.x; i < RB; i += RT) v += __ldcg(part + off + i);
   return block_sum(v);
+}
+
+// True in the block that finishes last (it then owns the final reduction).
+// The caller's thread 0 wrote its partial before; the fence orders it before
+// the count.
+__device__ __forceinline__ bool last_block(unsigned* done) {
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  return s_last;
 }
 
 __global__ void __launch_bounds__(RT) k_pcg_init(int64_t n, const int32_t* __restrict__ rowptr,
@@ -46,13 +64,13 @@ __global__ void __launch_bounds__(RT) k_pcg_init(int64_t n, const int32_t* __res
                                                  const double* __restrict__ b, double* __restrict__ x,
                                                  double* __restrict__ r, double* __restrict__ p,
                                                  double* __restrict__ dinv, double* __restrict__ part,
-                                                 unsigned* __restrict__ bad) {
+                                                 Scalars* __restrict__ sc) {
   double rz = 0.0, bb = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT) {
     double d = 0.0;
     for (int j = rowptr[i]; j < rowptr[i + 1]; ++j)
       if (colind[j] == i) d = val[j];
-    if (!(d > 0.0)) atomicOr(bad, 1u);
+    if (!(d > 0.0)) atomicOr(&sc->bad, 1u);
     const double di = d > 0.0 ? 1.0 / d : 0.0;
     const double bi = b[i];
     dinv[i] = di;
@@ -68,62 +86,157 @@ __global__ void __launch_bounds__(RT) k_pcg_init(int64_t n, const int32_t* __res
     part[RB + blockIdx.x] = rz;
     part[2 * RB + blockIdx.x] = bb;
   }
-}
-
-__global__ void __launch_bounds__(RT) k_init_scalars(const double* __restrict__ part, Scalars* sc) {
-  const double rz = sum_partials(part, RB);
-  const double bb = sum_partials(part, 2 * RB);
-  if (threadIdx.x == 0) {
-    sc->rz = rz;
-    sc->rz_next = rz;
-    sc->bb = bb;
-    sc->rr = bb;
+  if (last_block(&sc->done)) {
+    const double rz_t = sum_partials(part, RB);
+    const double bb_t = sum_partials(part, 2 * RB);
+    if (threadIdx.x == 0) {
+      sc->rz = rz_t;
+      sc->bb = bb_t;
+      sc->rr = bb_t;
+      sc->done = 0;
+    }
   }
 }
 
-// q = H p and the partial sums of p.q.  Block 0 first publishes the r.z of the
-// previous iteration (read by k_update, which runs after this kernel).
+// The solver keeps H in a slot-major ELL copy made once per solve: slot u of
+// row i at u n + i (column -1 past the row's end), W = the longest row.  A
+// warp's loads of slot u are then contiguous.  Rows of the condensed system
+// hold 4 or 7 entries, so the copy costs ~W/7 of the CSR bytes.
+constexpr int kEllMaxWidth = 16;  // wider rows keep the CSR kernel
+
+__global__ void k_row_width(int64_t n, const int32_t* __restrict__ rowptr, unsigned* __restrict__ wmax) {
+  unsigned w = 0;
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT)
+    w = max(w, (unsigned)(rowptr[i + 1] - rowptr[i]));
+  for (int o = 16; o > 0; o >>= 1) w = max(w, __shfl_down_sync(0xffffffffu, w, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(wmax, w);
+}
+
+__global__ void k_to_ell(int64_t n, int W, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                         const double* __restrict__ val, int32_t* __restrict__ ecol, double* __restrict__ eval) {
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT) {
+    const int j0 = rowptr[i], len = rowptr[i + 1] - j0;
+    for (int u = 0; u < W; ++u) {
+      ecol[u * n + i] = u < len ? colind[j0 + u] : -1;
+      eval[u * n + i] = u < len ? val[j0 + u] : 0.0;
+    }
+  }
+}
+
+// q = H p and p.q (ELL copy, one thread per row; the row sum is the fma chain
+// in column order); the last block sets alpha = r.z / p.q.
+template <int W>
+__global__ void __launch_bounds__(RT) k_spmv_dot_ell(int64_t n, int w, const int32_t* __restrict__ ecol,
+                                                     const double* __restrict__ eval, const double* __restrict__ p,
+                                                     double* __restrict__ q, double* __restrict__ part,
+                                                     Scalars* __restrict__ sc) {
+  double pq = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT) {
+    int c[W];
+    double v[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      c[u] = u < w ? __ldcs(ecol + u * n + i) : -1;
+      v[u] = u < w ? __ldcs(eval + u * n + i) : 0.0;
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int u = 0; u < W; ++u)
+      if (c[u] >= 0) s = fma(v[u], __ldg(p + c[u]), s);
+    q[i] = s;
+    pq = fma(__ldg(p + i), s, pq);
+  }
+  pq = block_sum(pq);
+  if (threadIdx.x == 0) part[blockIdx.x] = pq;
+  if (last_block(&sc->done)) {
+    const double pq_t = sum_partials(part, 0);
+    if (threadIdx.x == 0) {
+      sc->pq = pq_t;
+      sc->alpha = pq_t > 0.0 ? sc->rz / pq_t : 0.0;
+      sc->done = 0;
+    }
+  }
+}
+
+// The same on the CSR arrays, for rows wider than kEllMaxWidth: one thread per
+// row, the first 8 values and columns loaded at once (predicated) before the
+// gathers, longer rows finished in a loop.
 __global__ void __launch_bounds__(RT) k_spmv_dot(int64_t n, const int32_t* __restrict__ rowptr,
                                                  const int32_t* __restrict__ colind, const double* __restrict__ val,
                                                  const double* __restrict__ p, double* __restrict__ q,
                                                  double* __restrict__ part, Scalars* __restrict__ sc) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) sc->rz = sc->rz_next;
   double pq = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT) {
+    const int j0 = __ldg(rowptr + i), j1 = __ldg(rowptr + i + 1);
+    const int len = j1 - j0;
+    int c[8];
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      c[u] = u < len ? __ldg(colind + j0 + u) : 0;
+      v[u] = u < len ? __ldg(val + j0 + u) : 0.0;
+    }
     double s = 0.0;
-    for (int j = rowptr[i]; j < rowptr[i + 1]; ++j) s = fma(val[j], p[colind[j]], s);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (u < len) s = fma(v[u], __ldg(p + c[u]), s);
+    for (int j = j0 + 8; j < j1; ++j) s = fma(__ldg(val + j), __ldg(p + __ldg(colind + j)), s);
     q[i] = s;
-    pq = fma(p[i], s, pq);
+    pq = fma(__ldg(p + i), s, pq);
   }
   pq = block_sum(pq);
   if (threadIdx.x == 0) part[blockIdx.x] = pq;
+  if (last_block(&sc->done)) {
+    const double pq_t = sum_partials(part, 0);
+    if (threadIdx.x == 0) {
+      sc->pq = pq_t;
+      sc->alpha = pq_t > 0.0 ? sc->rz / pq_t : 0.0;
+      sc->done = 0;
+    }
+  }
 }
 
-// alpha = r.z / p.q (every block reduces the p.q partials itself), then
-// x += alpha p, r -= alpha q, and the partial sums of r.z (z = dinv r), r.r.
+// x += alpha p, r -= alpha q (pairs of entries per 16-byte access), and the
+// sums r.z (z = dinv r), r.r; the last block sets beta = r.z_new / r.z.
+template <bool VEC>
 __global__ void __launch_bounds__(RT) k_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
                                                const double* __restrict__ p, const double* __restrict__ q,
                                                const double* __restrict__ dinv, Scalars* __restrict__ sc,
                                                double* __restrict__ part) {
-  __shared__ double s_alpha;
-  const double pq = sum_partials(part, 0);
-  if (threadIdx.x == 0) {
-    const double alpha = pq > 0.0 ? sc->rz / pq : 0.0;
-    s_alpha = alpha;
-    if (blockIdx.x == 0) {
-      sc->pq = pq;
-      sc->alpha = alpha;
-    }
-  }
-  __syncthreads();
-  const double alpha = s_alpha;
+  const double alpha = sc->alpha;
   double rz = 0.0, rr = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT) {
-    x[i] = fma(alpha, p[i], x[i]);
-    const double ri = fma(-alpha, q[i], r[i]);
-    r[i] = ri;
-    rz = fma(ri, dinv[i] * ri, rz);
-    rr = fma(ri, ri, rr);
+  const int64_t stride = (int64_t)RB * RT;
+  if (VEC) {  // x 16-byte aligned; r, p, q, dinv always are
+    const int64_t n2 = n / 2;
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n2; i += stride) {
+      const double2 xi = reinterpret_cast<const double2*>(x)[i], pi = reinterpret_cast<const double2*>(p)[i];
+      const double2 qi = reinterpret_cast<const double2*>(q)[i], ri = reinterpret_cast<const double2*>(r)[i];
+      const double2 di = reinterpret_cast<const double2*>(dinv)[i];
+      const double2 xo = make_double2(fma(alpha, pi.x, xi.x), fma(alpha, pi.y, xi.y));
+      const double2 ro = make_double2(fma(-alpha, qi.x, ri.x), fma(-alpha, qi.y, ri.y));
+      __stcs(reinterpret_cast<double2*>(x) + i, xo);
+      reinterpret_cast<double2*>(r)[i] = ro;
+      rz = fma(ro.x, di.x * ro.x, rz);
+      rz = fma(ro.y, di.y * ro.y, rz);
+      rr = fma(ro.x, ro.x, rr);
+      rr = fma(ro.y, ro.y, rr);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+      const int64_t i = n - 1;
+      x[i] = fma(alpha, p[i], x[i]);
+      const double ri = fma(-alpha, q[i], r[i]);
+      r[i] = ri;
+      rz = fma(ri, dinv[i] * ri, rz);
+      rr = fma(ri, ri, rr);
+    }
+  } else {
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += stride) {
+      x[i] = fma(alpha, p[i], x[i]);
+      const double ri = fma(-alpha, q[i], r[i]);
+      r[i] = ri;
+      rz = fma(ri, dinv[i] * ri, rz);
+      rr = fma(ri, ri, rr);
+    }
   }
   rz = block_sum(rz);
   rr = block_sum(rr);
@@ -131,39 +244,123 @@ __global__ void __launch_bounds__(RT) k_update(int64_t n, double* __restrict__ x
     part[RB + blockIdx.x] = rz;
     part[2 * RB + blockIdx.x] = rr;
   }
-}
-
-// beta = r.z_new / r.z (every block reduces the partials itself; sc->rz is
-// only read here, the new value goes to sc->rz_next), then p = dinv r + beta p.
-__global__ void __launch_bounds__(RT) k_direction(int64_t n, double* __restrict__ p, const double* __restrict__ r,
-                                                  const double* __restrict__ dinv, Scalars* __restrict__ sc,
-                                                  const double* __restrict__ part) {
-  __shared__ double s_beta;
-  const double rz = sum_partials(part, RB);
-  const double rr = sum_partials(part, 2 * RB);
-  if (threadIdx.x == 0) {
-    const double rz_old = sc->rz;
-    s_beta = rz_old > 0.0 ? rz / rz_old : 0.0;
-    if (blockIdx.x == 0) {
-      sc->beta = s_beta;
-      sc->rr = rr;
-      sc->rz_next = rz;
+  if (last_block(&sc->done)) {
+    const double rz_t = sum_partials(part, RB);
+    const double rr_t = sum_partials(part, 2 * RB);
+    if (threadIdx.x == 0) {
+      const double rz_old = sc->rz;
+      sc->beta = rz_old > 0.0 ? rz_t / rz_old : 0.0;
+      sc->rz = rz_t;
+      sc->rr = rr_t;
+      sc->done = 0;
     }
   }
-  __syncthreads();
-  const double beta = s_beta;
-  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)RB * RT)
-    p[i] = fma(beta, p[i], dinv[i] * r[i]);
+}
+
+// p = dinv r + beta p (all workspace vectors: 16-byte pairs).
+__global__ void __launch_bounds__(RT) k_direction(int64_t n, double* __restrict__ p, const double* __restrict__ r,
+                                                  const double* __restrict__ dinv, const Scalars* __restrict__ sc) {
+  const double beta = sc->beta;
+  const int64_t n2 = (n + 1) / 2;  // vectors are padded to an even length
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n2; i += (int64_t)RB * RT) {
+    const double2 pi = reinterpret_cast<const double2*>(p)[i], ri = reinterpret_cast<const double2*>(r)[i];
+    const double2 di = reinterpret_cast<const double2*>(dinv)[i];
+    reinterpret_cast<double2*>(p)[i] = make_double2(fma(beta, pi.x, di.x * ri.x), fma(beta, pi.y, di.y * ri.y));
+  }
+}
+
+// H in the solver: the ELL copy when its rows are at most kEllMaxWidth wide.
+struct Matrix {
+  const int32_t *rowptr, *colind;
+  const double* values;
+  int w;  // ELL width, 0 = use the CSR arrays
+  const int32_t* ecol;
+  const double* eval;
+};
+
+inline void launch_spmv_dot(int64_t n, const Matrix& A, const double* p, double* q, double* part, Scalars* sc,
+                            cudaStream_t s) {
+  if (A.w == 0) k_spmv_dot<<<RB, RT, 0, s>>>(n, A.rowptr, A.colind, A.values, p, q, part, sc);
+  else if (A.w <= 4) k_spmv_dot_ell<4><<<RB, RT, 0, s>>>(n, A.w, A.ecol, A.eval, p, q, part, sc);
+  else if (A.w <= 7) k_spmv_dot_ell<7><<<RB, RT, 0, s>>>(n, A.w, A.ecol, A.eval, p, q, part, sc);
+  else k_spmv_dot_ell<kEllMaxWidth><<<RB, RT, 0, s>>>(n, A.w, A.ecol, A.eval, p, q, part, sc);
 }
 
 // one PCG iteration: 3 launches
-inline cudaError_t pcg_iteration(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* values,
-                                 double* x, double* r, double* p, double* q, const double* dinv, double* part,
-                                 Scalars* sc, cudaStream_t s) {
-  k_spmv_dot<<<RB, RT, 0, s>>>(n, rowptr, colind, values, p, q, part, sc);
-  k_update<<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
-  k_direction<<<RB, RT, 0, s>>>(n, p, r, dinv, sc, part);
+inline cudaError_t pcg_iteration(int64_t n, const Matrix& A, double* x, double* r, double* p, double* q,
+                                 const double* dinv, double* part, Scalars* sc, cudaStream_t s) {
+  launch_spmv_dot(n, A, p, q, part, sc, s);
+  if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) k_update<true><<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
+  else k_update<false><<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
+  k_direction<<<RB, RT, 0, s>>>(n, p, r, dinv, sc);
   return ph::launched(3);
+}
+
+// The solve proper on a given workspace (shared by both entry points).
+// ell_ok: the solve may allocate its ELL copy of H (not in the allocation-free entry point).
+ph_status pcg_run(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* values, const double* b,
+                  double* x, double rtol, int32_t maxit, int32_t* iters, double* relres, double* work,
+                  cudaStream_t s, bool ell_ok) {
+  const size_t nv = vec_stride(n);
+  double *r = work, *p = r + nv, *q = p + nv, *dinv = q + nv, *part = dinv + nv;
+  Scalars* sc = reinterpret_cast<Scalars*>(part + kPart);
+  Scalars h;
+  int it = 0;
+  Matrix A{rowptr, colind, values, 0, nullptr, nullptr};
+  void* ell = nullptr;
+  cudaError_t e = cudaMemsetAsync(sc, 0, sizeof(Scalars), s);
+  if (e == cudaSuccess && ell_ok) {  // width of the longest row (read at the first synchronisation below)
+    k_row_width<<<RB, RT, 0, s>>>(n, rowptr, &sc->done);
+    e = ph::launched();
+  }
+  // padding entries stay zero so the pairwise direction update is defined
+  if (e == cudaSuccess && nv > (size_t)n) e = cudaMemsetAsync(p + n, 0, sizeof(double) * (nv - n), s);
+  if (e == cudaSuccess && nv > (size_t)n) e = cudaMemsetAsync(r + n, 0, sizeof(double) * (nv - n), s);
+  if (e == cudaSuccess && nv > (size_t)n) e = cudaMemsetAsync(dinv + n, 0, sizeof(double) * (nv - n), s);
+  if (e == cudaSuccess && ell_ok) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && ell_ok) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && ell_ok && h.done <= (unsigned)kEllMaxWidth && h.done > 0) {
+    const int w = (int)h.done;
+    e = ph::alloc_bytes(&ell, (sizeof(double) + sizeof(int32_t)) * (size_t)w * (size_t)n + 16, s);
+    if (e == cudaSuccess) {
+      double* ev = static_cast<double*>(ell);
+      int32_t* ec = reinterpret_cast<int32_t*>(ev + (size_t)w * n);
+      k_to_ell<<<RB, RT, 0, s>>>(n, w, rowptr, colind, values, ec, ev);
+      e = ph::launched();
+      A = Matrix{rowptr, colind, values, w, ec, ev};
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(&sc->done, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) {
+    k_pcg_init<<<RB, RT, 0, s>>>(n, rowptr, colind, values, b, x, r, p, dinv, part, sc);
+    e = ph::launched();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || h.bad) {
+    if (ell) ph::free_async(ell, s);
+    return e != cudaSuccess ? ph::cuda_status(e, "pcg") : PH_ERR_ARG;
+  }
+  const double bnorm = sqrt(h.bb);
+  double res = bnorm;
+  while (res > rtol * bnorm && it < maxit) {
+    const int batch = (maxit - it) < 8 ? (maxit - it) : 8;
+    for (int i = 0; i < batch && e == cudaSuccess; ++i) e = pcg_iteration(n, A, x, r, p, q, dinv, part, sc, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      if (ell) ph::free_async(ell, s);
+      return ph::cuda_status(e, "pcg");
+    }
+    it += batch;
+    res = sqrt(h.rr);
+    if (iters) *iters = it;
+    if (h.pq <= 0.0 && res > rtol * bnorm) break;  // breakdown (H not SPD)
+  }
+  if (ell) ph::free_async(ell, s);
+  if (iters) *iters = it;
+  if (relres) *relres = bnorm > 0.0 ? res / bnorm : 0.0;
+  return res > rtol * bnorm ? PH_ERR_NOT_CONVERGED : PH_OK;
 }
 
 }  // namespace
@@ -180,49 +377,9 @@ extern "C" ph_status ph_solve_pcg(int64_t n, const int32_t* rowptr, const int32_
   if (!rowptr || !colind || !values || !b || !x) return PH_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   double* work = nullptr;
-  const size_t nvec = (size_t)n;
-  const size_t bytes = sizeof(double) * (4 * nvec + kPart) + sizeof(Scalars) + 16;
-  cudaError_t e = alloc_bytes(reinterpret_cast<void**>(&work), bytes, s);
+  cudaError_t e = alloc(&work, workspace_doubles(n), s);
   if (e != cudaSuccess) return cuda_status(e, "pcg alloc");
-  double *r = work, *p = r + nvec, *q = p + nvec, *dinv = q + nvec, *part = dinv + nvec;
-  Scalars* sc = reinterpret_cast<Scalars*>(part + kPart);
-  unsigned* bad = reinterpret_cast<unsigned*>(sc + 1);
-  ph_status st = PH_OK;
-  Scalars h;
-  unsigned hbad = 0;
-  int it = 0;
-  double bnorm = 0.0, res = 0.0;
-  e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s);
-  if (e == cudaSuccess) {
-    k_pcg_init<<<RB, RT, 0, s>>>(n, rowptr, colind, values, b, x, r, p, dinv, part, bad);
-    e = launched();
-  }
-  if (e == cudaSuccess) {
-    k_init_scalars<<<1, RT, 0, s>>>(part, sc);
-    e = launched();
-  }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) { st = cuda_status(e, "pcg"); goto done; }
-  if (hbad) { st = PH_ERR_ARG; goto done; }
-  bnorm = sqrt(h.bb);
-  res = bnorm;
-  while (res > rtol * bnorm && it < maxit) {
-    const int batch = (maxit - it) < 8 ? (maxit - it) : 8;
-    for (int i = 0; i < batch && e == cudaSuccess; ++i)
-      e = pcg_iteration(n, rowptr, colind, values, x, r, p, q, dinv, part, sc, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { st = cuda_status(e, "pcg"); goto done; }
-    it += batch;
-    res = sqrt(h.rr);
-    if (h.pq <= 0.0 && res > rtol * bnorm) break;  // breakdown (H not SPD)
-  }
-  if (iters) *iters = it;
-  if (relres) *relres = bnorm > 0.0 ? res / bnorm : 0.0;
-  if (res > rtol * bnorm) st = PH_ERR_NOT_CONVERGED;
-done:
+  const ph_status st = pcg_run(n, rowptr, colind, values, b, x, rtol, maxit, iters, relres, work, s, true);
   free_async(work, s);
   return st;
 }
@@ -255,8 +412,10 @@ extern "C" ph_status ph_spmv(int64_t n, const int32_t* rowptr, const int32_t* co
 
 #include <mutex>
 
-// r, p, q, dinv (4 n doubles), partial sums, scalars and the flag word.
-static constexpr size_t kNoAllocDoubles = 4 * (size_t)PH_PCG_NOALLOC_MAX_N + kPart + (sizeof(Scalars) + 16 + 7) / 8;
+// r, p, q, dinv (4 vectors of PH_PCG_NOALLOC_MAX_N doubles, a multiple of 32),
+// partial sums and scalars: the layout of workspace_doubles().
+static_assert(PH_PCG_NOALLOC_MAX_N % 32 == 0, "vector stride");
+static constexpr size_t kNoAllocDoubles = 4 * (size_t)PH_PCG_NOALLOC_MAX_N + kPart + (sizeof(Scalars) + 7) / 8;
 static __device__ __align__(256) double g_pcg_noalloc_work[kNoAllocDoubles];
 
 static std::mutex g_noalloc_mu;
@@ -295,43 +454,5 @@ extern "C" ph_status ph_solve_pcg_noalloc(int64_t n, const int32_t* rowptr, cons
   double* work = nullptr;
   ph_status st = noalloc_workspace(&work);
   if (st != PH_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
-  const size_t nvec = (size_t)n;
-  double *r = work, *p = r + nvec, *q = p + nvec, *dinv = q + nvec, *part = dinv + nvec;
-  Scalars* sc = reinterpret_cast<Scalars*>(part + kPart);
-  unsigned* bad = reinterpret_cast<unsigned*>(sc + 1);
-  Scalars h;
-  unsigned hbad = 0;
-  int it = 0;
-  double bnorm = 0.0, res = 0.0;
-  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s);  // the only word that must start at zero
-  if (e == cudaSuccess) {
-    k_pcg_init<<<RB, RT, 0, s>>>(n, rowptr, colind, values, b, x, r, p, dinv, part, bad);
-    e = launched();
-  }
-  if (e == cudaSuccess) {
-    k_init_scalars<<<1, RT, 0, s>>>(part, sc);
-    e = launched();
-  }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_status(e, "ph_solve_pcg_noalloc");
-  if (hbad) return PH_ERR_ARG;
-  bnorm = sqrt(h.bb);
-  res = bnorm;
-  while (res > rtol * bnorm && it < maxit) {
-    const int batch = (maxit - it) < 8 ? (maxit - it) : 8;
-    for (int i = 0; i < batch && e == cudaSuccess; ++i)
-      e = pcg_iteration(n, rowptr, colind, values, x, r, p, q, dinv, part, sc, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_status(e, "ph_solve_pcg_noalloc");
-    it += batch;
-    res = sqrt(h.rr);
-    if (h.pq <= 0.0 && res > rtol * bnorm) break;
-  }
-  if (iters) *iters = it;
-  if (relres) *relres = bnorm > 0.0 ? res / bnorm : 0.0;
-  return res > rtol * bnorm ? PH_ERR_NOT_CONVERGED : PH_OK;
+  return pcg_run(n, rowptr, colind, values, b, x, rtol, maxit, iters, relres, work, (cudaStream_t)stream, false);
 }
