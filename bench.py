@@ -72,7 +72,7 @@ def measured_peaks():
 # kernels timed with the library's CUDA events inside the timed region
 TIMED_KERNELS = ("k_assemble", "k_zero_diag", "k_recover_factored")
 # sources that k_assemble is compiled from
-ASSEMBLE_SOURCES = ("assemble.cu", "element.cuh", "ph_internal.cuh")
+ASSEMBLE_SOURCES = ("assemble.cu", "element.cuh", "fp64.cuh")
 
 
 def assemble_sources_sha256():

@@ -6,6 +6,7 @@
 
 #include <atomic>
 
+#include "fp64.cuh"
 #include "ph.h"
 
 // tmult encoding: multiplier id in bits 0..30, bit 31 = Dirichlet boundary
@@ -86,50 +87,6 @@ inline ph_status status_from_bits(unsigned bits) {
   for (int c = 1; c < 32; ++c)
     if (bits & (1u << c)) return (ph_status)c;
   return PH_OK;
-}
-
-// --- FP64 helpers ---------------------------------------------------------
-// On this part FP64 arithmetic issues at 2 operations per clock per SM, 1/32
-// of the integer ALU rate, and the element kernels are bound by it.  Sign
-// flips and range tests are therefore done on the bit pattern with integer
-// instructions (IEEE negation is a flip of the sign bit), and 1/x uses a
-// short Newton iteration instead of a correctly rounded divide.
-
-// n ? -x : x, bit-exact with IEEE negation
-__device__ __forceinline__ double neg_if(double x, bool n) {
-  const unsigned hi = (unsigned)__double2hiint(x) ^ ((unsigned)n << 31);
-  return __hiloint2double((int)hi, __double2loint(x));
-}
-__device__ __forceinline__ double negate(double x) { return neg_if(x, true); }
-
-// 0 < x < +inf (false for zeros, negatives, infinities and NaN)
-__device__ __forceinline__ bool pos_finite(double x) {
-  const long long b = __double_as_longlong(x);
-  return b > 0 && b < 0x7FF0000000000000LL;
-}
-
-// 1/x by the Newton-Raphson iteration for the reciprocal, y <- y + y (1 - x y)
-// (quadratic convergence), seeded from the single-precision hardware
-// approximation rcp.approx of the top 20 mantissa bits of x (relative error
-// below 2^-19, so two steps reach full double precision: relative error of
-// the result below 2^-52, i.e. within an ulp of the rounded quotient).
-// x outside [2^-1020, 2^1021) -- including zero, negative, infinite and NaN
-// x -- takes the IEEE divide.
-__device__ __forceinline__ double rcp_newton(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x);
-  const int ex = (int)(hi >> 20);  // biased exponent; >= 2048 when the sign bit is set
-  if (ex < 3 || ex > 2043) return 1.0 / x;
-  const float m = __uint_as_float(0x3F800000u | ((hi & 0x000FFFFFu) << 3));  // mantissa in [1, 2)
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(m));  // r in (0.5, 1]
-  const unsigned rb = __float_as_uint(r);
-  const int e_out = (int)(rb >> 23) - 127 - (ex - 1023) + 1023;  // in [2, 2043]
-  const unsigned yhi = ((unsigned)e_out << 20) | ((rb & 0x007FFFFFu) >> 3);
-  double y = __hiloint2double((int)yhi, (int)((rb & 0x7u) << 29));
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
 }
 
 constexpr int kThreads = 256;
