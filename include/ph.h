@@ -330,6 +330,35 @@ const char* ph_last_error_message(void);
 int64_t ph_launch_count(void);
 
 /*
+ * One pass of the whole path from and to HOST memory: upload the mesh and
+ * its data, build the mesh (Section 3.3), assemble and condense (Eq. schur,
+ * Algorithm 1), recover U = A^-1(B + C' Lambda) (Algorithm 1, second loop)
+ * and download the system.  Equivalent to ph_mesh_create + ph_csr_pattern +
+ * ph_assemble + ph_recover_factored + copies, with the copies overlapping the
+ * kernels on two library streams (data up while the mesh is built, the CSR
+ * pattern down while the system is assembled, values and rhs down while U is
+ * recovered).  Page-locked host buffers give full-speed, asynchronous copies;
+ * pageable ones work but are staged.
+ *   coord [nC*3], tet [nE*4], neumann [nN*3] or NULL: as ph_mesh_create.
+ *   nF, L, nnz: the counts of the mesh these tets build (ph_mesh_info of an
+ *     earlier build); they size the face data and the outputs, and a mismatch
+ *     with the build gives PH_ERR_ARG.
+ *   a [nE], c, f_face [nF], uD_face [nF] or NULL, gN_face [nF] or NULL: as
+ *     ph_assemble.  lambda [L] or NULL (with u NULL): the face values for the
+ *     recovery.
+ *   rowptr [L+1], colind [nnz], values [nnz], rhs [L], u [nE*4] or NULL:
+ *     host outputs.
+ * Device memory comes from the library's pool and is released before the
+ * call returns; the call returns when the outputs are on the host.  Errors as
+ * the entry points it stands for.
+ */
+ph_status ph_assemble_host(const double* coord, int64_t nC, const int32_t* tet, int64_t nE,
+                           const int32_t* neumann, int64_t nN, int64_t nF, int64_t L, int64_t nnz,
+                           const double* a, double c, const double* f_face, const double* uD_face,
+                           const double* gN_face, const double* lambda, int32_t* rowptr, int32_t* colind,
+                           double* values, double* rhs, double* u, void* stream);
+
+/*
  * Kernel timing, off by default.  While enabled, the library records a pair
  * of CUDA events around each launch of k_assemble, k_zero_diag, k_recover and
  * k_recover_factored on the stream it launches on (not while that stream is

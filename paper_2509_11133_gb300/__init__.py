@@ -33,7 +33,7 @@ EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces",
            "ph_adjoint_rhs", "ph_adjoint_grad", "ph_batch_create", "ph_batch_destroy", "ph_batch_bind",
            "ph_batch_assemble", "ph_batch_autotune", "ph_batch_set_config", "ph_batch_get_config",
            "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy", "ph_rcp", "ph_timing_enable",
-           "ph_kernel_time")
+           "ph_kernel_time", "ph_assemble_host")
 
 
 class PHError(RuntimeError):
@@ -94,6 +94,7 @@ def load(path: str | None = None):
         "ph_rcp": [P, I64, P, P],
         "ph_timing_enable": [ctypes.c_int],
         "ph_kernel_time": [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(D), ctypes.POINTER(I64)],
+        "ph_assemble_host": [P, I64, P, I64, P, I64, I64, I64, I64, P, D, P, P, P, P, P, P, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -329,6 +330,35 @@ class Mesh:
 
 def ph_mesh_create(coord, tet, neumann=None, stream=None) -> Mesh:
     return Mesh(coord, tet, neumann, stream)
+
+
+def _hptr(t):
+    """Address of a contiguous CPU tensor (host buffer), or None."""
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CPU tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def ph_assemble_host(coord, tet, a, c, f_face, counts, lam=None, uD_face=None, gN_face=None, neumann=None,
+                     out=None, stream=None):
+    """The whole path from and to host (CPU, ideally pinned) tensors.
+    ``counts`` = (nF, L, nnz) of the mesh; returns dict(rowptr, colind,
+    values, rhs[, u]) of CPU tensors (``out`` supplies them)."""
+    nF, L, nnz = (int(x) for x in counts)
+    nE = tet.shape[0]
+    if out is None:
+        out = {"rowptr": torch.empty(L + 1, dtype=torch.int32), "colind": torch.empty(nnz, dtype=torch.int32),
+               "values": torch.empty(nnz, dtype=torch.float64), "rhs": torch.empty(L, dtype=torch.float64)}
+        if lam is not None:
+            out["u"] = torch.empty((nE, 4), dtype=torch.float64)
+    _check(load().ph_assemble_host(_hptr(coord), coord.shape[0], _hptr(tet), nE, _hptr(neumann),
+                                   0 if neumann is None else neumann.shape[0], nF, L, nnz, _hptr(a), float(c),
+                                   _hptr(f_face), _hptr(uD_face), _hptr(gN_face), _hptr(lam), _hptr(out["rowptr"]),
+                                   _hptr(out["colind"]), _hptr(out["values"]), _hptr(out["rhs"]), _hptr(out.get("u")),
+                                   _stream(stream)), "ph_assemble_host")
+    return out
 
 
 def ph_timing_enable(on: bool = True):
