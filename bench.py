@@ -339,6 +339,9 @@ def gpu_arm(args, rank, world, local_rank):
     traffic = profile_traffic(nE)
     bpt = assemble_bytes_per_tet(nE, p.nC, nF)
     value = whole_job_rate(nE, world, ms_per_step)
+    cfg = workload_config(args.workload, p, world)
+    if (cfg["nF"], cfg["L"], cfg["nnz"]) != (nF, L, nnz):
+        raise RuntimeError(f"mesh counts {nF, L, nnz} differ from the closed forms {cfg['nF'], cfg['L'], cfg['nnz']}")
     line = {
         "metric": METRIC,
         "value": value,
@@ -352,16 +355,7 @@ def gpu_arm(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {
-            "workload": args.workload,
-            "mesh": f"Kuhn {p.info['m']}^3 unit cube, {p.info['k']} levels of the paper's 1->12 refinement",
-            "nE": nE, "nC": p.nC, "nF": nF, "L": L, "nnz": nnz,
-            "a": "exp(N(0,1)) per element, seed 2", "c": p.c, "f": "(3 pi^2 + 1) sin(pi x) sin(pi y) sin(pi z)",
-            "boundary": "zero Dirichlet",
-            "step": "ph_mesh_create + ph_assemble (with element factor) + ph_recover_factored (seeded Lambda)",
-            "l2": "512 MiB buffer written between timed steps (outside the step events)",
-            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-        },
+        "config": cfg,
         "phases_ms": {"mesh_create": float(np.mean(create_ms)), "assemble": float(np.mean(asm_ms)),
                       "recover": float(np.mean(rec_ms))},
         "kernels_ms": kern,
@@ -572,8 +566,29 @@ def cpu_baseline(p, budget_s=15.0, steps=1):
                       f"assembly+condensation (binary128 per element), recovery; {t:.2f} s per pass"}
 
 
+def workload_config(workload, p, world):
+    """The config object of both arms.  Counts of the all-Dirichlet Kuhn
+    mesh in closed form: 12 m^2 4^k boundary faces, nF = (4 nE + boundary)/2,
+    L = nF, nnz = nF + 12 nE (each checked against the device build in the
+    full-size tests)."""
+    m, k = p.info["m"], p.info["k"]
+    nE = p.nE
+    nF = (4 * nE + 12 * m * m * 4 ** k) // 2
+    return {
+        "workload": workload,
+        "mesh": f"Kuhn {m}^3 unit cube, {k} levels of the paper's 1->12 refinement",
+        "nE": nE, "nC": p.nC, "nF": nF, "L": nF, "nnz": nF + 12 * nE,
+        "a": "exp(N(0,1)) per element, seed 2", "c": p.c, "f": "(3 pi^2 + 1) sin(pi x) sin(pi y) sin(pi z)",
+        "boundary": "zero Dirichlet",
+        "step": "mesh build (faces, multipliers, CSR pattern, geometry) + assembly and condensation "
+                "(with element factor) + element recovery from a seeded Lambda",
+        "l2": "512 MiB buffer written between timed steps (outside the step events)",
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+    }
+
+
 def reference_arm(args):
-    p = meshgen.problem(WORKLOAD)
+    p = make_problem(args.workload)
     import oracle
     oracle.build()
     # size one step to ~budget seconds, then W + K steps
@@ -594,13 +609,13 @@ def reference_arm(args):
         times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
     value = n / (ms * 1e-3)
-    sample = (f"first {n} tets of the {WORKLOAD} mesh as a sub-mesh per step: faces, multipliers, CSR pattern, "
+    sample = (f"first {n} tets of the {args.workload} mesh as a sub-mesh per step: faces, multipliers, CSR pattern, "
               f"assembly+condensation, recovery (single-threaded C oracle, binary128 per element)")
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nE_sample": n, "c": p.c},
+        "config": workload_config(args.workload, p, 1),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
