@@ -285,6 +285,31 @@ ph_status ph_refined_copy(const ph_refined* r, double* coord, int32_t* tet, int3
 ph_status ph_refined_destroy(ph_refined* r, void* stream);
 
 /*
+ * Additive Schwarz preconditioner over edge patches for H (an addition: the
+ * paper solves with a direct method).  Patch e holds the multipliers of the
+ * faces around mesh edge e (edges numbered as Listing NumEdges), and
+ *     M = sum_e R_e' (R_e H R_e')^-1 R_e,
+ * applied in a fixed summation order (reproducible bit for bit).  H is
+ * dominated by the elementwise terms d_T d_T' / (c|T|) (Eq. schur with
+ * A^-1 = J/(c|T|) + ...), whose null space -- divergence-free face fluxes --
+ * is spanned by fields supported on edge patches, so M leaves a condition
+ * number growing like h^-2 instead of Jacobi's a / (c h^4).
+ * ph_schwarz_create: from a mesh and the values of its assembled H
+ *   (ph_assemble output; CSR pattern of the mesh).  Patch blocks wider than
+ *   16 use their diagonal.  Synchronises `stream` once.  PH_ERR_ARG when a
+ *   patch block is not positive definite.
+ * ph_solve_pcg_schwarz: conjugate gradients on H preconditioned by P;
+ *   arguments and results as ph_solve_pcg (n = L of the mesh).  P must come
+ *   from the same mesh and values; concurrent solves may share P.
+ * ph_schwarz_destroy: frees in stream order.
+ */
+typedef struct ph_schwarz ph_schwarz;
+ph_status ph_schwarz_create(const ph_mesh* mesh, const double* values, void* stream, ph_schwarz** out);
+ph_status ph_schwarz_destroy(ph_schwarz* P, void* stream);
+ph_status ph_solve_pcg_schwarz(const ph_mesh* mesh, const double* values, const ph_schwarz* P, const double* b,
+                               double* x, double rtol, int32_t maxit, int32_t* iters, double* relres, void* stream);
+
+/*
  * y = H x for a CSR matrix (rowptr [n+1], colind, values) and x [n], y [n]
  * (float64 device arrays).  One kernel, no synchronisation.
  */

@@ -33,7 +33,8 @@ EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces",
            "ph_adjoint_rhs", "ph_adjoint_grad", "ph_batch_create", "ph_batch_destroy", "ph_batch_bind",
            "ph_batch_assemble", "ph_batch_autotune", "ph_batch_set_config", "ph_batch_get_config",
            "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy", "ph_rcp", "ph_timing_enable",
-           "ph_kernel_time", "ph_assemble_host")
+           "ph_kernel_time", "ph_assemble_host", "ph_schwarz_create", "ph_schwarz_destroy",
+           "ph_solve_pcg_schwarz")
 
 
 class PHError(RuntimeError):
@@ -95,6 +96,9 @@ def load(path: str | None = None):
         "ph_timing_enable": [ctypes.c_int],
         "ph_kernel_time": [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(D), ctypes.POINTER(I64)],
         "ph_assemble_host": [P, I64, P, I64, P, I64, I64, I64, I64, P, D, P, P, P, P, P, P, P, P, P, P],
+        "ph_schwarz_create": [P, P, P, ctypes.POINTER(P)],
+        "ph_schwarz_destroy": [P, P],
+        "ph_solve_pcg_schwarz": [P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -177,6 +181,43 @@ def ph_solve_pcg_noalloc(rowptr, colind, values, rhs, x=None, rtol=1e-12, maxit=
 
 
 PH_PCG_NOALLOC_MAX_N = 262144
+
+
+class Schwarz:
+    """Edge-patch additive Schwarz preconditioner of a mesh's assembled H
+    (``values`` from ``Mesh.assemble``); ``solve`` runs PCG with it."""
+
+    def __init__(self, mesh, values, stream=None):
+        h = ctypes.c_void_p()
+        self._h = None
+        self.mesh = mesh
+        _check(load().ph_schwarz_create(mesh.handle, _ptr(values.contiguous()), _stream(stream), ctypes.byref(h)),
+               "ph_schwarz_create")
+        self._h = h
+
+    def solve(self, values, rhs, x=None, rtol=1e-12, maxit=20000, stream=None, check=True):
+        """Returns (x, iters, relres, status) as ph_solve_pcg."""
+        n = rhs.numel()
+        if x is None:
+            x = torch.empty(n, dtype=torch.float64, device=rhs.device)
+        it = ctypes.c_int32(0)
+        rr = ctypes.c_double(0)
+        code = load().ph_solve_pcg_schwarz(self.mesh.handle, _ptr(values), self._h, _ptr(rhs), _ptr(x), float(rtol),
+                                           int(maxit), ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+        if check:
+            _check(code, "ph_solve_pcg_schwarz")
+        return x, it.value, rr.value, code
+
+    def close(self, stream=None):
+        if self._h is not None:
+            load().ph_schwarz_destroy(self._h, _stream(stream))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ph_spmv(rowptr, colind, values, x, y=None, stream=None):

@@ -18,95 +18,10 @@
 #include <math.h>
 #include <string.h>
 
+#include "edges.cuh"
 #include "ph_internal.cuh"
 
 namespace {
-
-__device__ __forceinline__ int vget(int4 v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
-
-// local edge j: IJ, IK, IL, JK, JL, KL
-__device__ __forceinline__ void local_edge(int j, int& p, int& q) {
-  const int P[6] = {0, 0, 0, 1, 1, 2};
-  const int Q[6] = {1, 2, 3, 2, 3, 3};
-  p = P[j];
-  q = Q[j];
-}
-
-__device__ __forceinline__ bool valid_tet(int4 v, int64_t nC) {
-  bool in = v.x >= 0 && v.y >= 0 && v.z >= 0 && v.w >= 0 && v.x < nC && v.y < nC && v.z < nC && v.w < nC;
-  bool distinct = v.x != v.y && v.x != v.z && v.x != v.w && v.y != v.z && v.y != v.w && v.z != v.w;
-  return in && distinct;
-}
-
-__global__ void k_edge_count(const int4* __restrict__ tet, int64_t nE, int64_t nC, int32_t* __restrict__ cnt,
-                             unsigned* status) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nE) return;
-  const int4 v = tet[t];
-  if (!valid_tet(v, nC)) { ph_flag(status, PH_ERR_ARG); return; }
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    int p, q;
-    local_edge(j, p, q);
-    atomicAdd(&cnt[max(vget(v, p), vget(v, q))], 1);
-  }
-}
-
-// entry = (lo, slot)
-// Both kernels below return at once once an invalid tet was flagged: the
-// entries of such a mesh are incomplete and must not be dereferenced.
-__global__ void k_edge_fill(const int4* __restrict__ tet, int64_t nE, int64_t nC, const int32_t* __restrict__ start,
-                            int32_t* __restrict__ cnt, int2* __restrict__ entries, const unsigned* status) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nE || *status) return;
-  const int4 v = tet[t];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    int p, q;
-    local_edge(j, p, q);
-    const int a = vget(v, p), b = vget(v, q);
-    const int hi = max(a, b), lo = min(a, b);
-    const int pos = start[hi] + atomicSub(&cnt[hi], 1) - 1;
-    entries[pos] = make_int2(lo, (int)(6 * t + j));
-  }
-}
-
-// first[slot] = smallest slot with the same (lo, hi); the bucket of entry i is
-// found from its slot's tet (hi = max of the slot's endpoints).
-__global__ void k_edge_first(const int4* __restrict__ tet, const int2* __restrict__ entries, int64_t nent,
-                             const int32_t* __restrict__ start, int32_t* __restrict__ first, const unsigned* status) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nent || *status) return;
-  const int2 e = entries[i];
-  const int t = e.y / 6, j = e.y % 6;
-  int p, q;
-  local_edge(j, p, q);
-  const int4 v = tet[t];
-  const int hi = max(vget(v, p), vget(v, q));
-  const int lo = start[hi], end = start[hi + 1];
-  int m = e.y;
-  for (int k = lo; k < end; ++k) {
-    const int2 f = entries[k];
-    if (f.x == e.x && f.y < m) m = f.y;
-  }
-  first[e.y] = m;
-}
-
-__global__ void k_edge_newcount(const int32_t* __restrict__ first, int64_t nE, int32_t* __restrict__ ecount) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nE) return;
-  int c = 0;
-#pragma unroll
-  for (int j = 0; j < 6; ++j) c += first[6 * t + j] == (int)(6 * t + j);
-  ecount[t] = c;
-}
-
-// first occurrences before local edge j of tet t (inclusive of tets < t: ebase)
-__device__ __forceinline__ int rank_in_tet(const int32_t* __restrict__ first, int64_t t, int j) {
-  int r = 0;
-  for (int k = 0; k < j; ++k) r += first[6 * t + k] == (int)(6 * t + k);
-  return r;
-}
 
 // per tet: centroid and midpoint ids, coordinates, the 12 children, and the
 // midpoint id of every slot (for the boundary lists)
@@ -206,8 +121,8 @@ extern "C" ph_status ph_refine(const double* coord, int64_t nC, const int32_t* t
     return PH_ERR_OVERFLOW;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t nent = 6 * nE;
-  int32_t *cnt = nullptr, *start = nullptr, *first = nullptr, *ebase = nullptr, *mid_of_slot = nullptr;
-  int2* entries = nullptr;
+  int32_t* mid_of_slot = nullptr;
+  EdgeNumbering E;
   int64_t* d_tot = nullptr;
   unsigned* status = nullptr;
   ph_refined* r = new ph_refined();
@@ -224,28 +139,7 @@ extern "C" ph_status ph_refine(const double* coord, int64_t nC, const int32_t* t
   RF_CU(alloc(&status, 1, s));
   RF_CU(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
   RF_CU(alloc(&d_tot, 1, s));
-  RF_CU(alloc(&cnt, (size_t)nC + 1, s));
-  RF_CU(alloc(&start, (size_t)nC + 1, s));
-  RF_CU(alloc(&entries, (size_t)nent, s));
-  RF_CU(alloc(&first, (size_t)nent, s));
-  RF_CU(alloc(&ebase, (size_t)nE + 1, s));
-  RF_CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nC + 1), s));
-  if (nE > 0) {
-    k_edge_count<<<grid_for(nE), kThreads, 0, s>>>(reinterpret_cast<const int4*>(tet), nE, nC, cnt, status);
-    RF_CU(launched());
-  }
-  st = exclusive_scan(cnt, start, nC + 1, d_tot, s, status);
-  if (st != PH_OK) goto fail;
-  if (nE > 0) {
-    k_edge_fill<<<grid_for(nE), kThreads, 0, s>>>(reinterpret_cast<const int4*>(tet), nE, nC, start, cnt, entries,
-                                                status);
-    k_edge_first<<<grid_for(nent), kThreads, 0, s>>>(reinterpret_cast<const int4*>(tet), entries, nent, start, first,
-                                                     status);
-    k_edge_newcount<<<grid_for(nE), kThreads, 0, s>>>(first, nE, ebase);
-    RF_CU(launched(3));
-  }
-  RF_CU(cudaMemsetAsync(ebase + nE, 0, sizeof(int32_t), s));
-  st = exclusive_scan(ebase, ebase, nE + 1, d_tot, s, status);
+  st = enqueue_edges(reinterpret_cast<const int4*>(tet), nE, nC, status, d_tot, s, &E);
   if (st != PH_OK) goto fail;
   RF_CU(cudaMemcpyAsync(&tot, d_tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   RF_CU(cudaMemcpyAsync(&bits, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -262,22 +156,19 @@ extern "C" ph_status ph_refine(const double* coord, int64_t nC, const int32_t* t
   RF_CU(alloc(&mid_of_slot, (size_t)nent, s));
   if (nC > 0) RF_CU(cudaMemcpyAsync(r->coord, coord, sizeof(double) * 3 * nC, cudaMemcpyDeviceToDevice, s));
   if (nE > 0) {
-    k_refine_tets<<<grid_for(nE), kThreads, 0, s>>>(coord, reinterpret_cast<const int4*>(tet), nE, nC, first, ebase,
+    k_refine_tets<<<grid_for(nE), kThreads, 0, s>>>(coord, reinterpret_cast<const int4*>(tet), nE, nC, E.first, E.ebase,
                                                     r->coord, r->tet, mid_of_slot);
     RF_CU(launched());
   }
   if (nl > 0) {
-    k_refine_lists<<<grid_for(nl), kThreads, 0, s>>>(lists, nl, entries, start, mid_of_slot, nC, r->lists, status);
+    k_refine_lists<<<grid_for(nl), kThreads, 0, s>>>(lists, nl, E.entries, E.start, mid_of_slot, nC, r->lists,
+                                                     status);
     RF_CU(launched());
   }
   RF_CU(cudaMemcpyAsync(&bits, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   RF_CU(cudaStreamSynchronize(s));
   if (bits) { st = status_from_bits(bits); goto fail; }
-  free_async(cnt, s);
-  free_async(start, s);
-  free_async(entries, s);
-  free_async(first, s);
-  free_async(ebase, s);
+  release_edges(E, s);
   free_async(mid_of_slot, s);
   free_async(d_tot, s);
   free_async(status, s);
@@ -286,11 +177,7 @@ extern "C" ph_status ph_refine(const double* coord, int64_t nC, const int32_t* t
 cuda_fail:
   st = cuda_status(e, "ph_refine");
 fail:
-  free_async(cnt, s);
-  free_async(start, s);
-  free_async(entries, s);
-  free_async(first, s);
-  free_async(ebase, s);
+  release_edges(E, s);
   free_async(mid_of_slot, s);
   free_async(d_tot, s);
   free_async(status, s);

@@ -4,60 +4,18 @@
 // solves are bitwise reproducible.
 #include <math.h>
 
+#include "pcg.cuh"
 #include "ph_internal.cuh"
 
 namespace {
 
-constexpr int RT = 256;   // threads per block
-constexpr int RB = 1216;  // blocks (8 x 152 SMs) for vector kernels and partial sums
-
-struct Scalars {
-  double rz, pq, alpha, beta, rr, bb;
-  unsigned done;  // blocks finished in the current reducing kernel (last-block detection)
-  unsigned bad;   // a non-positive diagonal entry was seen
-};
+using namespace ph_pcg;
 
 // Workspace of one solve (doubles): r, p, q, dinv (4 vectors of vec_stride(n)
-// doubles, so each starts 256-byte aligned), then the partial sums
-// part[0, RB) = p.q, part[RB, 2RB) = r.z, part[2RB, 3RB) = r.r, then Scalars.
-constexpr size_t kPart = 3 * (size_t)RB;
+// doubles, so each starts 256-byte aligned), then the partial sums, then
+// Scalars.
 inline size_t vec_stride(int64_t n) { return ((size_t)n + 31) & ~(size_t)31; }
 inline size_t workspace_doubles(int64_t n) { return 4 * vec_stride(n) + kPart + (sizeof(Scalars) + 7) / 8; }
-
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double sm[RT / 32];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (threadIdx.x < 32) {
-    r = threadIdx.x < RT / 32 ? sm[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-  }
-  __syncthreads();
-  return r;  // valid in thread 0
-}
-
-// Sum of part[off, off + RB) in a fixed order (every caller gets the same
-// value); the partials come from other blocks, so they bypass L1.
-__device__ __forceinline__ double sum_partials(const double* __restrict__ part, int off) {
-  double v = 0.0;
-  for (int i = threadIdx.x; i < RB; i += RT) v += __ldcg(part + off + i);
-  return block_sum(v);
-}
-
-// True in the block that finishes last (it then owns the final reduction).
-// The caller's thread 0 wrote its partial before; the fence orders it before
-// the count.
-__device__ __forceinline__ bool last_block(unsigned* done) {
-  __shared__ bool s_last;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  return s_last;
-}
 
 __global__ void __launch_bounds__(RT) k_pcg_init(int64_t n, const int32_t* __restrict__ rowptr,
                                                  const int32_t* __restrict__ colind, const double* __restrict__ val,
@@ -197,8 +155,10 @@ __global__ void __launch_bounds__(RT) k_spmv_dot(int64_t n, const int32_t* __res
 }
 
 // x += alpha p, r -= alpha q (pairs of entries per 16-byte access), and the
-// sums r.z (z = dinv r), r.r; the last block sets beta = r.z_new / r.z.
-template <bool VEC>
+// sums r.r and (Jacobi, JAC) r.z with z = dinv r; the last block sets rr and
+// (JAC) beta = r.z_new / r.z.  With another preconditioner z and beta come
+// from its application.
+template <bool VEC, bool JAC>
 __global__ void __launch_bounds__(RT) k_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
                                                const double* __restrict__ p, const double* __restrict__ q,
                                                const double* __restrict__ dinv, Scalars* __restrict__ sc,
@@ -211,13 +171,15 @@ __global__ void __launch_bounds__(RT) k_update(int64_t n, double* __restrict__ x
     for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n2; i += stride) {
       const double2 xi = reinterpret_cast<const double2*>(x)[i], pi = reinterpret_cast<const double2*>(p)[i];
       const double2 qi = reinterpret_cast<const double2*>(q)[i], ri = reinterpret_cast<const double2*>(r)[i];
-      const double2 di = reinterpret_cast<const double2*>(dinv)[i];
+      const double2 di = JAC ? reinterpret_cast<const double2*>(dinv)[i] : make_double2(0.0, 0.0);
       const double2 xo = make_double2(fma(alpha, pi.x, xi.x), fma(alpha, pi.y, xi.y));
       const double2 ro = make_double2(fma(-alpha, qi.x, ri.x), fma(-alpha, qi.y, ri.y));
       __stcs(reinterpret_cast<double2*>(x) + i, xo);
       reinterpret_cast<double2*>(r)[i] = ro;
-      rz = fma(ro.x, di.x * ro.x, rz);
-      rz = fma(ro.y, di.y * ro.y, rz);
+      if (JAC) {
+        rz = fma(ro.x, di.x * ro.x, rz);
+        rz = fma(ro.y, di.y * ro.y, rz);
+      }
       rr = fma(ro.x, ro.x, rr);
       rr = fma(ro.y, ro.y, rr);
     }
@@ -226,7 +188,7 @@ __global__ void __launch_bounds__(RT) k_update(int64_t n, double* __restrict__ x
       x[i] = fma(alpha, p[i], x[i]);
       const double ri = fma(-alpha, q[i], r[i]);
       r[i] = ri;
-      rz = fma(ri, dinv[i] * ri, rz);
+      if (JAC) rz = fma(ri, dinv[i] * ri, rz);
       rr = fma(ri, ri, rr);
     }
   } else {
@@ -234,7 +196,7 @@ __global__ void __launch_bounds__(RT) k_update(int64_t n, double* __restrict__ x
       x[i] = fma(alpha, p[i], x[i]);
       const double ri = fma(-alpha, q[i], r[i]);
       r[i] = ri;
-      rz = fma(ri, dinv[i] * ri, rz);
+      if (JAC) rz = fma(ri, dinv[i] * ri, rz);
       rr = fma(ri, ri, rr);
     }
   }
@@ -245,15 +207,28 @@ __global__ void __launch_bounds__(RT) k_update(int64_t n, double* __restrict__ x
     part[2 * RB + blockIdx.x] = rr;
   }
   if (last_block(&sc->done)) {
-    const double rz_t = sum_partials(part, RB);
+    const double rz_t = JAC ? sum_partials(part, RB) : 0.0;
     const double rr_t = sum_partials(part, 2 * RB);
     if (threadIdx.x == 0) {
-      const double rz_old = sc->rz;
-      sc->beta = rz_old > 0.0 ? rz_t / rz_old : 0.0;
-      sc->rz = rz_t;
+      if (JAC) {
+        const double rz_old = sc->rz;
+        sc->beta = rz_old > 0.0 ? rz_t / rz_old : 0.0;
+        sc->rz = rz_t;
+      }
       sc->rr = rr_t;
       sc->done = 0;
     }
+  }
+}
+
+// p = z + beta p for a preconditioned residual z held in memory.
+__global__ void __launch_bounds__(RT) k_direction_z(int64_t n, double* __restrict__ p, const double* __restrict__ z,
+                                                    const Scalars* __restrict__ sc) {
+  const double beta = sc->beta;
+  const int64_t n2 = (n + 1) / 2;  // vectors are padded to an even length
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n2; i += (int64_t)RB * RT) {
+    const double2 pi = reinterpret_cast<const double2*>(p)[i], zi = reinterpret_cast<const double2*>(z)[i];
+    reinterpret_cast<double2*>(p)[i] = make_double2(fma(beta, pi.x, zi.x), fma(beta, pi.y, zi.y));
   }
 }
 
@@ -286,21 +261,37 @@ inline void launch_spmv_dot(int64_t n, const Matrix& A, const double* p, double*
   else k_spmv_dot_ell<kEllMaxWidth><<<RB, RT, 0, s>>>(n, A.w, A.ecol, A.eval, p, q, part, sc);
 }
 
-// one PCG iteration: 3 launches
+// one PCG iteration: 3 launches (Jacobi, z = dinv r fused), or 5 with the
+// Schwarz preconditioner P (z kept in the dinv vector, y its scratch)
 inline cudaError_t pcg_iteration(int64_t n, const Matrix& A, double* x, double* r, double* p, double* q,
-                                 const double* dinv, double* part, Scalars* sc, cudaStream_t s) {
+                                 double* dinv, double* part, Scalars* sc, const ph_schwarz* P, double* y,
+                                 cudaStream_t s) {
   launch_spmv_dot(n, A, p, q, part, sc, s);
-  if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) k_update<true><<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
-  else k_update<false><<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
-  k_direction<<<RB, RT, 0, s>>>(n, p, r, dinv, sc);
-  return ph::launched(3);
+  const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+  if (!P) {
+    if (vec) k_update<true, true><<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
+    else k_update<false, true><<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
+    k_direction<<<RB, RT, 0, s>>>(n, p, r, dinv, sc);
+    return ph::launched(3);
+  }
+  if (vec) k_update<true, false><<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
+  else k_update<false, false><<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
+  cudaError_t e = ph::launched(2);
+  if (e == cudaSuccess) e = schwarz_apply(P, r, dinv, y, part, sc, false, s);
+  if (e == cudaSuccess) {
+    k_direction_z<<<RB, RT, 0, s>>>(n, p, dinv, sc);
+    e = ph::launched();
+  }
+  return e;
 }
 
 // The solve proper on a given workspace (shared by both entry points).
-// ell_ok: the solve may allocate its ELL copy of H (not in the allocation-free entry point).
+// ell_ok: the solve may allocate its ELL copy of H (not in the allocation-free
+// entry point).  P: Schwarz preconditioner (y: its scratch of P->nmem
+// doubles), or null for Jacobi.
 ph_status pcg_run(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* values, const double* b,
                   double* x, double rtol, int32_t maxit, int32_t* iters, double* relres, double* work,
-                  cudaStream_t s, bool ell_ok) {
+                  cudaStream_t s, bool ell_ok, const ph_schwarz* P = nullptr, double* y = nullptr) {
   const size_t nv = vec_stride(n);
   double *r = work, *p = r + nv, *q = p + nv, *dinv = q + nv, *part = dinv + nv;
   Scalars* sc = reinterpret_cast<Scalars*>(part + kPart);
@@ -335,6 +326,13 @@ ph_status pcg_run(int64_t n, const int32_t* rowptr, const int32_t* colind, const
     k_pcg_init<<<RB, RT, 0, s>>>(n, rowptr, colind, values, b, x, r, p, dinv, part, sc);
     e = ph::launched();
   }
+  if (e == cudaSuccess && P) {  // z = M b, p = z
+    e = schwarz_apply(P, r, dinv, y, part, sc, true, s);
+    if (e == cudaSuccess) {
+      k_direction_z<<<RB, RT, 0, s>>>(n, p, dinv, sc);
+      e = ph::launched();
+    }
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess || h.bad) {
@@ -345,7 +343,8 @@ ph_status pcg_run(int64_t n, const int32_t* rowptr, const int32_t* colind, const
   double res = bnorm;
   while (res > rtol * bnorm && it < maxit) {
     const int batch = (maxit - it) < 8 ? (maxit - it) : 8;
-    for (int i = 0; i < batch && e == cudaSuccess; ++i) e = pcg_iteration(n, A, x, r, p, q, dinv, part, sc, s);
+    for (int i = 0; i < batch && e == cudaSuccess; ++i)
+      e = pcg_iteration(n, A, x, r, p, q, dinv, part, sc, P, y, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -380,6 +379,26 @@ extern "C" ph_status ph_solve_pcg(int64_t n, const int32_t* rowptr, const int32_
   cudaError_t e = alloc(&work, workspace_doubles(n), s);
   if (e != cudaSuccess) return cuda_status(e, "pcg alloc");
   const ph_status st = pcg_run(n, rowptr, colind, values, b, x, rtol, maxit, iters, relres, work, s, true);
+  free_async(work, s);
+  return st;
+}
+
+extern "C" ph_status ph_solve_pcg_schwarz(const ph_mesh* m, const double* values, const ph_schwarz* P,
+                                          const double* b, double* x, double rtol, int32_t maxit, int32_t* iters,
+                                          double* relres, void* stream) {
+  if (iters) *iters = 0;
+  if (relres) *relres = 0.0;
+  if (!m || !P || P->L != m->L || !(rtol >= 0.0) || maxit < 0) return PH_ERR_ARG;
+  const int64_t n = m->L;
+  if (n == 0) return PH_OK;
+  if (!values || !b || !x) return PH_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* work = nullptr;
+  const size_t wd = workspace_doubles(n);
+  cudaError_t e = alloc(&work, wd + (size_t)P->nmem, s);
+  if (e != cudaSuccess) return cuda_status(e, "pcg alloc");
+  const ph_status st =
+      pcg_run(n, m->rowptr, m->colind, values, b, x, rtol, maxit, iters, relres, work, s, true, P, work + wd);
   free_async(work, s);
   return st;
 }
