@@ -518,24 +518,39 @@ class Batch:
             pass
 
 
+def solve_system(mesh, values, rhs, rtol, maxit, precond="schwarz", P=None):
+    """H Lambda = rhs on the mesh's CSR pattern: PCG with the edge-patch
+    Schwarz preconditioner (P reused when given) or Jacobi.  Returns
+    (Lambda, iterations, P)."""
+    if precond == "schwarz":
+        P = Schwarz(mesh, values) if P is None else P
+        lam, it, _, _ = P.solve(values, rhs, rtol=rtol, maxit=maxit)
+        return lam, it, P
+    if precond != "jacobi":
+        raise ValueError("precond: 'schwarz' or 'jacobi'")
+    rowptr, colind = mesh.csr_pattern()
+    lam, it, _, _ = ph_solve_pcg(rowptr, colind, values, rhs, rtol=rtol, maxit=maxit)
+    return lam, it, None
+
+
 class MisfitFunction(torch.autograd.Function):
     """J(log a) = 1/2 sum_T e_T' M(T) e_T, e = U(a) - U_obs, through assembly,
     condensation, the PCG solve and recovery; backward is the hand-written
-    adjoint (ph_adjoint_rhs, a second solve with the same H, ph_adjoint_grad).
+    adjoint (ph_adjoint_rhs, a second solve with the same H -- and the same
+    preconditioner -- and ph_adjoint_grad).
 
-    apply(log_a, mesh, c, f_face, u_obs, uD_face, gN_face, rtol, maxit)
+    apply(log_a, mesh, c, f_face, u_obs, uD_face, gN_face, rtol, maxit, precond)
     """
 
     @staticmethod
-    def forward(ctx, log_a, mesh, c, f_face, u_obs, uD_face=None, gN_face=None, rtol=1e-12, maxit=50000):
+    def forward(ctx, log_a, mesh, c, f_face, u_obs, uD_face=None, gN_face=None, rtol=1e-12, maxit=50000,
+                precond="schwarz"):
         a = torch.exp(log_a)
-        rowptr, colind = mesh.csr_pattern()
         values, rhs, factor = mesh.assemble(a, c, f_face, uD_face, gN_face, factor=True)
-        lam, _, _, _ = ph_solve_pcg(rowptr, colind, values, rhs, rtol=rtol, maxit=maxit)
+        lam, _, P = solve_system(mesh, values, rhs, rtol, maxit, precond)
         u = mesh.recover_factored(factor, c, f_face, lam, gN_face)
         J = mesh.misfit(u, u_obs)
-        ctx.mesh, ctx.c, ctx.rtol, ctx.maxit = mesh, c, rtol, maxit
-        ctx.csr = (rowptr, colind)
+        ctx.mesh, ctx.c, ctx.rtol, ctx.maxit, ctx.precond, ctx.P = mesh, c, rtol, maxit, precond, P
         ctx.save_for_backward(a, values, factor, u, u_obs)
         return J
 
@@ -544,11 +559,14 @@ class MisfitFunction(torch.autograd.Function):
         a, values, factor, u, u_obs = ctx.saved_tensors
         mesh = ctx.mesh
         rhs_q = mesh.adjoint_rhs(factor, ctx.c, u, u_obs)
-        q, _, _, _ = ph_solve_pcg(*ctx.csr, values, rhs_q, rtol=ctx.rtol, maxit=ctx.maxit)
+        q, _, _ = solve_system(mesh, values, rhs_q, ctx.rtol, ctx.maxit, ctx.precond, ctx.P)
         grad = mesh.adjoint_grad(a, factor, ctx.c, u, u_obs, q)
-        return gJ * grad, None, None, None, None, None, None, None, None
+        if ctx.P is not None:
+            ctx.P.close()
+            ctx.P = None
+        return gJ * grad, None, None, None, None, None, None, None, None, None
 
 
-def misfit(log_a, mesh, c, f_face, u_obs, uD_face=None, gN_face=None, rtol=1e-12, maxit=50000):
+def misfit(log_a, mesh, c, f_face, u_obs, uD_face=None, gN_face=None, rtol=1e-12, maxit=50000, precond="schwarz"):
     """Differentiable misfit (see MisfitFunction)."""
-    return MisfitFunction.apply(log_a, mesh, c, f_face, u_obs, uD_face, gN_face, rtol, maxit)
+    return MisfitFunction.apply(log_a, mesh, c, f_face, u_obs, uD_face, gN_face, rtol, maxit, precond)

@@ -4,11 +4,11 @@ and against central finite differences.
 
 Full-size checks use the adjoint workload (Kuhn 6^3 cube refined 3 levels,
 2,239,488 tets, c = 0.1, U_obs from a lognormal a with seed 5, gradient at a
-lognormal a with seed 51): a Taylor check along a random direction.
-Central differences on 20 random elements run by default on the same recipe
-on a Kuhn 3^3 cube refined 3 levels (279,936 tets), since each needs four
-global solves; PH_FD_FULLSIZE=1 runs them on the full adjoint workload.  Each
-difference is computed by difference solves: with a' = a except
+lognormal a with seed 51): a Taylor check along a random direction, and
+central differences on 20 random elements (four global solves each, with the
+edge-patch Schwarz preconditioner; PH_FD_SMALL=1 runs them on a 279,936-tet
+mesh of the same recipe instead).  Each difference is computed by difference
+solves: with a' = a except
 a'_t = a_t e^{+-eps},
       H' dLambda = dr - dH Lambda        (dr, dH: element t's changes only),
       dU = A'^-1 C' dLambda  (plus element t's own change of A^-1),
@@ -57,21 +57,31 @@ class Setup:
         self.a = cu(a)
         self.U_obs = cu(U_obs)
 
-    def forward(self, a, rtol=1e-12):
+    precond = "schwarz"
+
+    def solve(self, values, rhs, rtol, P=None):
+        lam, it, P = self.ph.solve_system(self.mesh, values, rhs, rtol, 200000, self.precond, P)
+        return lam, it, P
+
+    def forward(self, a, rtol=1e-12, keep_P=False):
         m = self.mesh
         values, rhs, factor = m.assemble(a, self.p.c, self.f, self.uD, self.gN, factor=True)
-        lam, it, rr, _ = self.ph.ph_solve_pcg(self.rowptr, self.colind, values, rhs, rtol=rtol, maxit=200000,
-                                             check=False)
+        lam, it, P = self.solve(values, rhs, rtol)
         u = m.recover_factored(factor, self.p.c, self.f, lam, self.gN)
-        return dict(values=values, rhs=rhs, factor=factor, lam=lam, u=u, J=m.misfit(u, self.U_obs), iters=it,
-                    relres=rr)
+        out = dict(values=values, rhs=rhs, factor=factor, lam=lam, u=u, J=m.misfit(u, self.U_obs), iters=it)
+        if keep_P:
+            out["P"] = P
+        elif P is not None:
+            P.close()
+        return out
 
     def gradient(self, a, rtol=1e-12):
-        fw = self.forward(a, rtol)
+        fw = self.forward(a, rtol, keep_P=True)
         m = self.mesh
         rq = m.adjoint_rhs(fw["factor"], self.p.c, fw["u"], self.U_obs)
-        q, _, _, _ = self.ph.ph_solve_pcg(self.rowptr, self.colind, fw["values"], rq, rtol=rtol, maxit=200000,
-                                          check=False)
+        q, _, P = self.solve(fw["values"], rq, rtol, fw.pop("P"))
+        if P is not None:
+            P.close()
         g = m.adjoint_grad(a, fw["factor"], self.p.c, fw["u"], self.U_obs, q)
         return fw, g
 
@@ -83,8 +93,9 @@ def obs_field(ph, p, seed):
     return u
 
 
+@pytest.mark.parametrize("precond", ["schwarz", "jacobi"])
 @pytest.mark.parametrize("case", ["kuhn_m1_k1", "paper_mixed1", "kuhn_m2_k1"])
-def test_adjoint_matches_oracle(ph, case):
+def test_adjoint_matches_oracle(ph, case, precond):
     if case == "paper_mixed1":
         p = meshgen.problem("paper_mixed", 1)
     else:
@@ -93,6 +104,7 @@ def test_adjoint_matches_oracle(ph, case):
     U_obs = obs_field(ph, p, 51)
     a = meshgen.lognormal_field(p.nE, 5)
     s = Setup(ph, p, a, U_obs)
+    s.precond = precond
     fw, g = s.gradient(s.a)
     J_o, g_o, U_o, _ = oracle.adjoint_gradient(p.coord, p.tet, a, p.c, p.f, U_obs, p.uD, p.gN, p.neumann)
     assert abs(fw["J"].item() - J_o) <= 1e-9 * abs(J_o)
@@ -207,7 +219,9 @@ def _difference_solve(s, fw, t, eps):
     rho = (r2[l] - r1[l]) - dS @ lam[l]
     rhs_loc = torch.zeros(m.L, dtype=torch.float64, device="cuda")
     rhs_loc[torch.as_tensor(l, device="cuda")] = cu(rho)
-    dlam, it, rr, _ = ph.ph_solve_pcg(s.rowptr, s.colind, values2, rhs_loc, rtol=BIG_RTOL, maxit=200000, check=False)
+    dlam, _, P = s.solve(values2, rhs_loc, BIG_RTOL)
+    if P is not None:
+        P.close()
     zero_f = torch.zeros_like(s.f)
     dU = m.recover_factored(factor2, p.c, zero_f, dlam).cpu().numpy()
     # element t: its own A changes too
@@ -218,10 +232,12 @@ def _difference_solve(s, fw, t, eps):
 
 @pytest.fixture(scope="module")
 def fd_case(ph, big):
+    """The full adjoint workload (PH_FD_SMALL=1: the 279,936-tet mesh of the
+    same recipe, for a quick run)."""
     import os
-    if os.environ.get("PH_FD_FULLSIZE") == "1":
-        return big
-    return make_adjoint_setup(ph, "kuhn_m3_k3")
+    if os.environ.get("PH_FD_SMALL") == "1":
+        return make_adjoint_setup(ph, "kuhn_m3_k3")
+    return big
 
 
 def test_central_differences_20_elements(fd_case):
