@@ -64,13 +64,25 @@ cudaError_t schwarz_apply(const ph_schwarz* P, const double* r, double* z, doubl
 
 // Additive Schwarz preconditioner over edge patches: patch e holds the
 // multipliers of the faces around edge e; M = sum_e R_e' (R_e H R_e')^-1 R_e.
+// Patches are grouped by their number of members k (a patch wider than
+// kSchwarzDense becomes k patches of one member: its diagonal), and within a
+// group every array is slot-major (entry q of patch s at base + q count + s),
+// so the threads of a warp -- consecutive patches of one group -- make
+// contiguous accesses.
+constexpr int kSchwarzDense = 16;  // widest patch inverted densely
+
+struct SchwarzGroups {
+  int64_t count[kSchwarzDense + 1];  // patches with k members
+  int64_t first[kSchwarzDense + 2];  // index of the first patch of group k (patches ordered by k)
+  int64_t mbase[kSchwarzDense + 1];  // group k in mem and y: k slots per patch
+  int64_t bbase[kSchwarzDense + 1];  // group k in blk: k(k+1)/2 entries per patch
+};
+
 struct ph_schwarz {
   int device;
-  int64_t L, nEd, nmem;
-  int32_t* off;    // nEd+1: members of patch e at mem[off[e], off[e+1])
-  int32_t* mem;    // nmem: multiplier ids, ascending within a patch
-  int32_t* boff;   // nEd+1: block offsets in blk (doubles)
-  double* blk;     // patch inverses (upper triangle, row-major), 1/diag for patches wider than kSchwarzDense
-  int32_t* fslot;  // 3L: positions in mem of each multiplier in the patches of its face's three edges
+  int64_t L, nEd, nmem, npatch, nblk;
+  SchwarzGroups g;
+  int32_t* mem;    // multiplier ids, ascending within a patch
+  double* blk;     // patch inverses: packed upper triangle, row-major
+  int32_t* fslot;  // 3L: positions in mem (and y) of each multiplier in the patches of its face's three edges
 };
-constexpr int kSchwarzDense = 16;  // widest patch inverted densely
