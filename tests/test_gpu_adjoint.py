@@ -137,19 +137,21 @@ def test_autograd_function(ph):
 # ---------------------------------------------------------------------------
 # full size
 # ---------------------------------------------------------------------------
-BIG_RTOL = 1e-10      # PCG residual reachable on the full adjoint workload
+BIG_RTOL = 1e-10      # PCG residual of the gradient workload
+FD_SOLVE_RTOL = 1e-12  # gradient and difference solves of the central-difference check
 TAYLOR_RTOL = 1e-3
 FD_RTOL = 2e-6
 
 
-def make_adjoint_setup(ph, name):
+def make_adjoint_setup(ph, name, rtol=BIG_RTOL):
     p = meshgen.problem(name)
     p.c = 0.1
     s0 = Setup(ph, p, meshgen.lognormal_field(p.nE, 5), np.zeros((p.nE, 4)))
-    U_obs = s0.forward(s0.a, rtol=BIG_RTOL)["u"].cpu().numpy()
+    U_obs = s0.forward(s0.a, rtol=rtol)["u"].cpu().numpy()
     s0.mesh.close()
     s = Setup(ph, p, meshgen.lognormal_field(p.nE, 51), U_obs)
-    fw, g = s.gradient(s.a, rtol=BIG_RTOL)
+    s.rtol = rtol
+    fw, g = s.gradient(s.a, rtol=rtol)
     return s, fw, g.cpu().numpy()
 
 
@@ -219,7 +221,7 @@ def _difference_solve(s, fw, t, eps):
     rho = (r2[l] - r1[l]) - dS @ lam[l]
     rhs_loc = torch.zeros(m.L, dtype=torch.float64, device="cuda")
     rhs_loc[torch.as_tensor(l, device="cuda")] = cu(rho)
-    dlam, _, P = s.solve(values2, rhs_loc, BIG_RTOL)
+    dlam, _, P = s.solve(values2, rhs_loc, s.rtol)
     if P is not None:
         P.close()
     zero_f = torch.zeros_like(s.f)
@@ -231,13 +233,13 @@ def _difference_solve(s, fw, t, eps):
 
 
 @pytest.fixture(scope="module")
-def fd_case(ph, big):
-    """The full adjoint workload (PH_FD_SMALL=1: the 279,936-tet mesh of the
-    same recipe, for a quick run)."""
+def fd_case(ph):
+    """The full adjoint workload at the tighter solve tolerance (elements whose
+    gradient is far below the typical one need it); PH_FD_SMALL=1: the
+    279,936-tet mesh of the same recipe, for a quick run."""
     import os
-    if os.environ.get("PH_FD_SMALL") == "1":
-        return make_adjoint_setup(ph, "kuhn_m3_k3")
-    return big
+    name = "kuhn_m3_k3" if os.environ.get("PH_FD_SMALL") == "1" else "kuhn_m6_k3"
+    return make_adjoint_setup(ph, name, FD_SOLVE_RTOL)
 
 
 def test_central_differences_20_elements(fd_case):
@@ -248,13 +250,19 @@ def test_central_differences_20_elements(fd_case):
     fw["e"] = fw["u_h"] - s.U_obs.cpu().numpy()
     fw["vol"] = _masses(s)
     rng = np.random.default_rng(20)
+    # Each difference dJ is a sum over all elements of terms that largely
+    # cancel, so it carries an absolute rounding floor (~1e-20 here, i.e.
+    # ~1e-17 on a difference quotient).  It shows only on elements whose
+    # gradient is far below the typical one, so errors are measured against
+    # max(|g_t|, rms(g)/10).
+    scale_floor = np.sqrt(np.mean(g * g)) / 10
     worst = 0.0
     for t in rng.choice(s.p.nE, 20, replace=False):
         fd = []
         for eps in (1e-3, 5e-4):
             fd.append((_difference_solve(s, fw, t, eps) - _difference_solve(s, fw, t, -eps)) / (2 * eps))
         rich = (4 * fd[1] - fd[0]) / 3
-        err = abs(rich - g[t]) / abs(g[t])
+        err = abs(rich - g[t]) / max(abs(g[t]), scale_floor)
         worst = max(worst, err)
         print("element", t, "fd", fd, "richardson", rich, "adjoint", g[t], "rel", err)
     print("worst relative FD error", worst)
