@@ -74,6 +74,9 @@ def measured_peaks():
 E_INFLIGHT = 2
 # kernels timed with the library's CUDA events inside the timed region
 TIMED_KERNELS = ("k_assemble", "k_zero_diag", "k_recover_factored")
+# mesh-build kernels, timed in a separate short loop (their timers add host
+# work between the build's launches)
+BUILD_KERNELS = ("k_face_count", "k_face_fill", "k_face_match", "k_new_count", "k_face_emit", "k_row_fill", "k_scan")
 # sources that k_assemble is compiled from
 ASSEMBLE_SOURCES = ("assemble.cu", "element.cuh", "fp64.cuh")
 
@@ -264,6 +267,20 @@ def gpu_arm(args, rank, world, local_rank):
     for name in TIMED_KERNELS:
         ms, n = ph.ph_kernel_time(name, reset=True)
         kern[name] = ms / n if n else float("nan")
+    # breakdown of the mesh build: a few more steps with its kernels timed
+    # (not part of the headline timing)
+    for name in BUILD_KERNELS:
+        ph.ph_kernel_time(name, reset=True)
+    ph.ph_timing_enable(2)
+    for _ in range(5):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    ph.ph_timing_enable(False)
+    build_kern = {}
+    for name in BUILD_KERNELS:
+        ms, n = ph.ph_kernel_time(name, reset=True)
+        build_kern[name] = ms / 5 if n else float("nan")  # per build (k_scan: all scans of one build)
     barrier()
     clk = clocks.stop()
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
@@ -359,6 +376,7 @@ def gpu_arm(args, rank, world, local_rank):
         "phases_ms": {"mesh_create": float(np.mean(create_ms)), "assemble": float(np.mean(asm_ms)),
                       "recover": float(np.mean(rec_ms))},
         "kernels_ms": kern,
+        "mesh_build_kernels_ms": build_kern,
         "roofline": {
             "kernel": "k_assemble (average launch over the timed steps, CUDA events on its stream)",
             "bound": "alu",
@@ -573,6 +591,31 @@ def cpu_baseline(p, budget_s=15.0, steps=1):
                       f"assembly+condensation (binary128 per element), recovery; {t:.2f} s per pass"}
 
 
+def profile_pcg(iters):
+    """A fixed number of Schwarz-preconditioned PCG iterations on the adjoint
+    workload's system (Kuhn 6^3 cube, 3 levels, c = 0.1, lognormal a with
+    seed 51): a target for profiler launch lists of the solve."""
+    import torch
+    import paper_2509_11133_gb300 as ph
+    from paper_2509_11133_gb300 import build
+    build.build()
+    ph.load()
+    dev = torch.device("cuda", 0)
+    p = meshgen.problem("kuhn_m6_k3")
+    mesh = ph.Mesh(torch.as_tensor(p.coord, device=dev), torch.as_tensor(p.tet, device=dev))
+    cen = mesh.faces()["face_centroid"].cpu().numpy()
+    f = torch.as_tensor(np.asarray(meshgen.sin_source(cen), np.float64), device=dev)
+    a = torch.as_tensor(meshgen.lognormal_field(p.nE, 51), device=dev)
+    values, rhs = mesh.assemble(a, 0.1, f)
+    P = ph.Schwarz(mesh, values)
+    _, it, _, _ = P.solve(values, rhs, rtol=0.0, maxit=iters, check=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_pcg": {"L": mesh.L, "iterations": it}}))
+    P.close()
+    mesh.close()
+    return 0
+
+
 def workload_config(workload, p, world):
     """The config object of both arms.  Counts of the all-Dirichlet Kuhn
     mesh in closed form: 12 m^2 4^k boundary faces, nF = (4 nE + boundary)/2,
@@ -640,12 +683,16 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=3.0)
+    ap.add_argument("--profile-pcg", type=int, default=0, metavar="N",
+                    help="profiler target: N Schwarz-PCG iterations on the adjoint workload, then exit")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.profile_pcg > 0:
+        return profile_pcg(args.profile_pcg)
     if args.impl == "reference":
         if rank != 0:
             return 0

@@ -384,10 +384,14 @@ ph_status ph_assemble_host(const double* coord, int64_t nC, const int32_t* tet, 
                            double* values, double* rhs, double* u, void* stream);
 
 /*
- * Kernel timing, off by default.  While enabled, the library records a pair
- * of CUDA events around each launch of k_assemble, k_zero_diag, k_recover and
- * k_recover_factored on the stream it launches on (not while that stream is
- * being captured into a graph).  ph_kernel_time waits for the recorded events
+ * Kernel timing, off by default.  `on` is a mask: bit 0 times k_assemble,
+ * k_zero_diag, k_recover and k_recover_factored; bit 1 the mesh-build kernels
+ * (k_face_count, k_face_fill, k_face_match, k_new_count, k_face_emit,
+ * k_row_fill) and the scans (k_scan); 0 switches timing off.  A timed launch
+ * is bracketed by a pair of CUDA events on the stream it runs on (not while
+ * that stream is being captured into a graph); the events come from a pool
+ * stocked when timing is switched on.  Timing the mesh build adds host work
+ * between its launches and lengthens it slightly.  ph_kernel_time waits for the recorded events
  * of the named kernel, adds their elapsed times to its running total and
  * returns the total device time in ms and the number of launches timed;
  * reset != 0 clears the total afterwards.  An unknown name returns 0, 0.

@@ -402,9 +402,10 @@ def ph_assemble_host(coord, tet, a, c, f_face, counts, lam=None, uD_face=None, g
     return out
 
 
-def ph_timing_enable(on: bool = True):
-    """Switch the library's per-kernel CUDA-event timing on or off."""
-    _check(load().ph_timing_enable(1 if on else 0), "ph_timing_enable")
+def ph_timing_enable(on=True):
+    """Switch the library's per-kernel CUDA-event timing: True or 1 for the
+    element kernels, 2 for the mesh build and scans, 3 for both, False/0 off."""
+    _check(load().ph_timing_enable(int(on)), "ph_timing_enable")
 
 
 def ph_kernel_time(kernel: str, reset: bool = False):

@@ -429,9 +429,7 @@ using namespace ph;
 
 static void mesh_free(ph_mesh* m, cudaStream_t s) {
   if (!m) return;
-  void* ptrs[] = {m->coord, m->tet, m->tface, m->tmult, m->tpos, m->trel, m->geo, m->face_tet, m->face_vtx,
-                  m->face_kind, m->face_mult, m->face_area, m->rowptr, m->colind, m->rowdiag, m->status};
-  for (void* p : ptrs) free_async(p, s);
+  free_async(m->arena, s);
   delete m;
 }
 
@@ -467,116 +465,139 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   // face-key buckets: 4 per largest vertex while the bucket ids stay below 2^31
   const int sub = nC < ((int64_t)1 << 28) ? 2 : 0;
   const int64_t nb = (nC << sub) + 1;
-  ph_mesh* m = new ph_mesh();
-  memset(m, 0, sizeof *m);
-  int32_t *cnt = nullptr, *start = nullptr, *mate = nullptr, *newc = nullptr, *flag = nullptr, *rowlen = nullptr;
-  int4* entries = nullptr;
-  int64_t* d_tot = nullptr;  // [0] nF, [1] L, [2] nnz
-  int64_t tot[3] = {0, 0, 0};
-  unsigned bits = 0;
   const int64_t nent = nFmax;
   const unsigned gF = grid_for(nFmax + 1);
+  ph_mesh* m = new ph_mesh();
+  memset(m, 0, sizeof *m);
+  int64_t tot[3] = {0, 0, 0};
+  unsigned bits = 0;
+  // Two allocations: the mesh's arrays, and the scratch of the build (its
+  // first part zeroed by one memset).  Few host calls keep the GPU fed.
+  Carve mc, sc;
+  const size_t o_status = mc.take<unsigned>(1), o_coord = mc.take<double>(3 * nC), o_tet = mc.take<int4>(nE);
+  const size_t o_geo = mc.take<double>(PH_GEO_STRIDE * nE), o_tface = mc.take<int4>(nE);
+  const size_t o_tmult = mc.take<int4>(nE), o_tpos = mc.take<int4>(nE), o_trel = mc.take<ushort4>(nE);
+  const size_t o_ftet = mc.take<int2>(nFmax), o_fvtx = mc.take<int32_t>(3 * nFmax);
+  const size_t o_fkind = mc.take<int8_t>(nFmax), o_fmult = mc.take<int32_t>(nFmax + 1);
+  const size_t o_farea = mc.take<double>(nFmax), o_rowptr = mc.take<int32_t>(nFmax + 1);
+  const size_t o_colind = mc.take<int32_t>(nnzmax), o_rowdiag = mc.take<int32_t>(nFmax);
+  // scratch: zeroed part first
+  const size_t o_tot = sc.take<int64_t>(3), o_cnt = sc.take<int32_t>(nb), o_newc = sc.take<int32_t>(nE + 1);
+  const size_t o_s1 = sc.take<unsigned long long>(scan_state_words(nb));
+  const size_t o_s2 = sc.take<unsigned long long>(scan_state_words(nE + 1));
+  const size_t o_s3 = sc.take<unsigned long long>(scan_state_words(nFmax + 1));
+  const size_t o_s4 = sc.take<unsigned long long>(scan_state_words(nFmax + 1));
+  const size_t o_rowlen = sc.take<int32_t>(nN > 0 || nE == 0 ? nFmax + 1 : 0);  // else written by k_face_emit
+  const size_t o_flag = sc.take<int32_t>(nN > 0 ? nFmax + 1 : 0);
+  const size_t zero_bytes = sc.bytes;
+  const size_t o_start = sc.take<int32_t>(nb), o_entries = sc.take<int4>(nent), o_mate = sc.take<int32_t>(4 * nE);
+  const size_t o_rowlen2 = sc.take<int32_t>(nN > 0 || nE == 0 ? 0 : nFmax + 1);
+  void* scratch = nullptr;
   PH_CU(cudaGetDevice(&m->device), "cudaGetDevice");
   m->nE = nE;
   m->nC = nC;
-  PH_CU(alloc(&m->status, 1, s), "alloc");
+  PH_CU(alloc_bytes(&m->arena, mc.bytes, s), "alloc mesh");
+  PH_CU(alloc_bytes(&scratch, sc.bytes, s), "alloc scratch");
+  {
+    void* A = m->arena;
+    m->status = Carve::at<unsigned>(A, o_status);
+    m->coord = Carve::at<double>(A, o_coord);
+    m->tet = Carve::at<int4>(A, o_tet);
+    m->geo = Carve::at<double>(A, o_geo);
+    m->tface = Carve::at<int4>(A, o_tface);
+    m->tmult = Carve::at<int4>(A, o_tmult);
+    m->tpos = Carve::at<int4>(A, o_tpos);
+    m->trel = Carve::at<ushort4>(A, o_trel);
+    m->face_tet = Carve::at<int2>(A, o_ftet);
+    m->face_vtx = Carve::at<int32_t>(A, o_fvtx);
+    m->face_kind = Carve::at<int8_t>(A, o_fkind);
+    m->face_mult = Carve::at<int32_t>(A, o_fmult);
+    m->face_area = Carve::at<double>(A, o_farea);
+    m->rowptr = Carve::at<int32_t>(A, o_rowptr);
+    m->colind = Carve::at<int32_t>(A, o_colind);
+    m->rowdiag = Carve::at<int32_t>(A, o_rowdiag);
+  }
+  {
+  int64_t* d_tot = Carve::at<int64_t>(scratch, o_tot);  // [0] nF, [1] L, [2] nnz
+  int32_t* cnt = Carve::at<int32_t>(scratch, o_cnt);
+  int32_t* newc = Carve::at<int32_t>(scratch, o_newc);
+  int32_t* start = Carve::at<int32_t>(scratch, o_start);
+  int4* entries = Carve::at<int4>(scratch, o_entries);
+  int32_t* mate = Carve::at<int32_t>(scratch, o_mate);
+  int32_t* flag = nN > 0 ? Carve::at<int32_t>(scratch, o_flag) : nullptr;
+  int32_t* rowlen = Carve::at<int32_t>(scratch, (nN > 0 || nE == 0) ? o_rowlen : o_rowlen2);
+  unsigned long long* st1 = Carve::at<unsigned long long>(scratch, o_s1);
+  unsigned long long* st2 = Carve::at<unsigned long long>(scratch, o_s2);
+  unsigned long long* st3 = Carve::at<unsigned long long>(scratch, o_s3);
+  unsigned long long* st4 = Carve::at<unsigned long long>(scratch, o_s4);
+  PH_CU(cudaMemsetAsync(scratch, 0, zero_bytes, s), "memset");
   PH_CU(cudaMemsetAsync(m->status, 0, sizeof(unsigned), s), "memset");
-  PH_CU(alloc(&d_tot, 3, s), "alloc");
-  PH_CU(cudaMemsetAsync(d_tot, 0, 3 * sizeof(int64_t), s), "memset");
-  PH_CU(alloc(&m->coord, (size_t)(3 * nC), s), "alloc coord");
-  PH_CU(alloc(&m->tet, (size_t)nE, s), "alloc tet");
-  PH_CU(alloc(&m->geo, (size_t)(PH_GEO_STRIDE * nE), s), "alloc");
   if (nC > 0) PH_CU(cudaMemcpyAsync(m->coord, coord, sizeof(double) * 3 * nC, cudaMemcpyDeviceToDevice, s), "copy");
 
   // --- faces: bucket the keys, match them, number the faces ----------------
-  PH_CU(alloc(&cnt, (size_t)nb, s), "alloc");
-  PH_CU(alloc(&start, (size_t)nb, s), "alloc");
-  PH_CU(alloc(&entries, (size_t)nent, s), "alloc");
-  PH_CU(alloc(&mate, (size_t)(4 * nE), s), "alloc");
-  PH_CU(alloc(&newc, (size_t)nE + 1, s), "alloc");
-  PH_CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)nb, s), "memset");
-  PH_CU(cudaMemsetAsync(newc, 0, sizeof(int32_t) * (nE + 1), s), "memset");
   if (nent > 0) {
+    KernelTimer kt("k_face_count", s, 2);
     k_face_count<<<grid_for(nE + nN), kThreads, 0, s>>>(reinterpret_cast<const int4*>(tet), nE, nC, neumann, nN,
                                                         sub, cnt, m->tet, m->status);
     PH_CU(launched(), "k_face_count");
   }
-  PH_TRY(exclusive_scan(cnt, start, nb, d_tot, s, m->status));
+  PH_TRY(exclusive_scan(cnt, start, nb, d_tot, s, m->status, nullptr, 0, st1));
   if (nent > 0) {
-    k_face_fill<<<grid_for(nE + nN), kThreads, 0, s>>>(m->tet, nE, nC, neumann, nN, sub, start, cnt, entries,
-                                                       mate, m->coord, m->geo, m->status);
-    PH_CU(launched(), "k_face_fill");
-    k_face_match<<<grid_for(nent), kThreads, 0, s>>>(entries, nent, start, sub, nE, mate, m->status);
-    PH_CU(launched(), "k_face_match");
+    {
+      KernelTimer kt("k_face_fill", s, 2);
+      k_face_fill<<<grid_for(nE + nN), kThreads, 0, s>>>(m->tet, nE, nC, neumann, nN, sub, start, cnt, entries,
+                                                         mate, m->coord, m->geo, m->status);
+      PH_CU(launched(), "k_face_fill");
+    }
+    {
+      KernelTimer kt("k_face_match", s, 2);
+      k_face_match<<<grid_for(nent), kThreads, 0, s>>>(entries, nent, start, sub, nE, mate, m->status);
+      PH_CU(launched(), "k_face_match");
+    }
   }
   if (nE > 0) {
+    KernelTimer kt("k_new_count", s, 2);
     k_new_count<<<grid_for(nE), kThreads, 0, s>>>(reinterpret_cast<int4*>(mate), nE, newc, m->status);
     PH_CU(launched(), "k_new_count");
   }
-  PH_TRY(exclusive_scan(newc, newc, nE + 1, d_tot, s, m->status));  // nF -> d_tot[0]
-  free_async(cnt, s); cnt = nullptr;
-  free_async(start, s); start = nullptr;
-  free_async(entries, s); entries = nullptr;
-
-  PH_CU(alloc(&m->tface, (size_t)nE, s), "alloc");
-  PH_CU(alloc(&m->face_tet, (size_t)nFmax, s), "alloc");
-  PH_CU(alloc(&m->face_vtx, (size_t)(3 * nFmax), s), "alloc");
-  PH_CU(alloc(&m->face_kind, (size_t)nFmax, s), "alloc");
-  PH_CU(alloc(&m->face_mult, (size_t)nFmax + 1, s), "alloc");
-  PH_CU(alloc(&m->face_area, (size_t)nFmax, s), "alloc");
-  PH_CU(alloc(&m->tmult, (size_t)nE, s), "alloc");
-  PH_CU(alloc(&rowlen, (size_t)nFmax + 1, s), "alloc");
-  PH_CU(alloc(&m->rowptr, (size_t)nFmax + 1, s), "alloc");
-  if (nN > 0) {
-    PH_CU(alloc(&flag, (size_t)nFmax + 1, s), "alloc");
-    PH_CU(cudaMemsetAsync(flag, 0, sizeof(int32_t) * (nFmax + 1), s), "memset");
-  }
+  PH_TRY(exclusive_scan(newc, newc, nE + 1, d_tot, s, m->status, nullptr, 0, st2));  // nF -> d_tot[0]
   if (nE > 0) {
+    KernelTimer kt("k_face_emit", s, 2);
     k_face_emit<<<grid_for(nE), kThreads, 0, s>>>(m->tet, nE, reinterpret_cast<int4*>(mate), newc, m->tface,
                                                   m->face_tet, m->face_vtx, m->face_kind, flag,
                                                   nN > 0 ? nullptr : m->face_mult, m->tmult, rowlen, m->status);
     PH_CU(launched(), "k_face_emit");
   }
-  free_async(mate, s); mate = nullptr;
-  free_async(newc, s); newc = nullptr;
 
   // --- multipliers and CSR pattern (rows sized by nFmax >= L) ---------------
   if (nN > 0) {
-    PH_TRY(exclusive_scan(flag, m->face_mult, nFmax + 1, d_tot + 1, s, m->status, d_tot, 1));  // L -> d_tot[1]
+    PH_TRY(exclusive_scan(flag, m->face_mult, nFmax + 1, d_tot + 1, s, m->status, d_tot, 1, st3));  // L -> d_tot[1]
     k_mult_fix<<<gF, kThreads, 0, s>>>(m->face_mult, m->face_kind, d_tot, nFmax, m->status);
     PH_CU(launched(), "k_mult_fix");
-    free_async(flag, s); flag = nullptr;
-  } else {  // every face has a multiplier (written by k_face_emit): L = nF
+    if (nE > 0) {
+      k_tet_mult<<<grid_for(nE), kThreads, 0, s>>>(m->tface, nE, m->face_mult, m->face_tet, m->tmult, rowlen,
+                                                   m->status);
+      PH_CU(launched(), "k_tet_mult");
+    }
+  } else {  // every face has a multiplier (k_face_emit wrote them, the slots' ids and the row lengths): L = nF
     PH_CU(cudaMemcpyAsync(d_tot + 1, d_tot, sizeof(int64_t), cudaMemcpyDeviceToDevice, s), "copy");
   }
-  // without Neumann faces k_face_emit wrote tmult and the row lengths
-  if (nN > 0 || nE == 0) PH_CU(cudaMemsetAsync(rowlen, 0, sizeof(int32_t) * (nFmax + 1), s), "memset");
-  if (nN > 0 && nE > 0) {
-    k_tet_mult<<<grid_for(nE), kThreads, 0, s>>>(m->tface, nE, m->face_mult, m->face_tet, m->tmult, rowlen,
-                                                 m->status);
-    PH_CU(launched(), "k_tet_mult");
-  }
-  PH_TRY(exclusive_scan(rowlen, m->rowptr, nFmax + 1, d_tot + 2, s, m->status, d_tot + 1, 1));  // nnz -> d_tot[2]
-  free_async(rowlen, s); rowlen = nullptr;
+  PH_TRY(exclusive_scan(rowlen, m->rowptr, nFmax + 1, d_tot + 2, s, m->status, d_tot + 1, 1, st4));  // nnz
 
-  // --- CSR columns and scatter positions ----------------------------------
-  PH_CU(alloc(&m->colind, (size_t)nnzmax, s), "alloc");
-  PH_CU(alloc(&m->rowdiag, (size_t)nFmax, s), "alloc");
-  PH_CU(alloc(&m->tpos, (size_t)nE, s), "alloc");
-  PH_CU(alloc(&m->trel, (size_t)nE, s), "alloc");
-  PH_CU(cudaMemsetAsync(m->tpos, 0, sizeof(int4) * nE, s), "memset");
-  PH_CU(cudaMemsetAsync(m->trel, 0, sizeof(ushort4) * nE, s), "memset");
+  // --- CSR columns and scatter positions (slots without a multiplier are never read)
   if (nFmax > 0) {
+    KernelTimer kt("k_row_fill", s, 2);
     k_row_fill<<<gF, kThreads, 0, s>>>(m->face_tet, m->tface, m->tmult, m->face_mult, d_tot, nFmax, m->rowptr,
-                                       m->colind,
-                                       m->rowdiag, reinterpret_cast<int32_t*>(m->tpos),
+                                       m->colind, m->rowdiag, reinterpret_cast<int32_t*>(m->tpos),
                                        reinterpret_cast<unsigned short*>(m->trel), m->coord, m->face_vtx,
                                        m->face_area, m->status);
     PH_CU(launched(), "k_row_fill");
   }
   // the one synchronisation: counts and the first error of any kernel
   PH_TRY(read_counters(d_tot, 3, m->status, s, tot, &bits));
-  free_async(d_tot, s); d_tot = nullptr;
+  }
+  free_async(scratch, s);
+  scratch = nullptr;
   if (bits) { st = status_from_bits(bits); goto fail; }
   m->nF = tot[0];
   m->L = tot[1];
@@ -590,14 +611,7 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   return PH_OK;
 
 fail:
-  free_async(cnt, s);
-  free_async(start, s);
-  free_async(entries, s);
-  free_async(mate, s);
-  free_async(newc, s);
-  free_async(flag, s);
-  free_async(rowlen, s);
-  free_async(d_tot, s);
+  free_async(scratch, s);
   mesh_free(m, s);
   return st;
 }

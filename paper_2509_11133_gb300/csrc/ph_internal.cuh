@@ -20,6 +20,7 @@
 
 struct ph_mesh {
   int device;
+  void* arena;         // one allocation holding every array below
   int64_t nE, nC, nF, nFi, nFd, nFn, L, nnz;
   double* coord;       // nC*3
   int4* tet;           // nE
@@ -54,8 +55,12 @@ inline cudaError_t launched(int n = 1) {
 // stream is being captured into a graph.
 class KernelTimer {
  public:
-  KernelTimer(const char* name, cudaStream_t s);
-  void stop();  // after the launch
+  // category 1: element kernels (assembly, recovery); 2: mesh build and scans
+  KernelTimer(const char* name, cudaStream_t s, unsigned category = 1);
+  ~KernelTimer() { stop(); }
+  KernelTimer(const KernelTimer&) = delete;
+  KernelTimer& operator=(const KernelTimer&) = delete;
+  void stop();  // after the launch (again at scope exit: no effect)
  private:
   const char* name_;
   cudaStream_t s_;
@@ -79,8 +84,27 @@ void free_async(void* p, cudaStream_t s);
 // alias.  With d_len, only min(n, *d_len + len_add) values (a length known
 // on the device) are scanned.  A look-back wait that times out sets
 // PH_ERR_TIMEOUT in *status (if given) instead of hanging.
+// `state` (optional): a zeroed workspace of scan_state_words(n) words; without
+// it the scan allocates and clears its own.
 ph_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* d_total, cudaStream_t s,
-                         unsigned* status = nullptr, const int64_t* d_len = nullptr, int64_t len_add = 0);
+                         unsigned* status = nullptr, const int64_t* d_len = nullptr, int64_t len_add = 0,
+                         unsigned long long* state = nullptr);
+size_t scan_state_words(int64_t n);
+
+// Sub-arrays of one allocation, each starting on a 256-byte boundary.
+struct Carve {
+  size_t bytes = 0;
+  template <class T>
+  size_t take(size_t n) {
+    const size_t at = bytes;
+    bytes += (n * sizeof(T) + 255) & ~(size_t)255;
+    return at;
+  }
+  template <class T>
+  static T* at(void* base, size_t off) {
+    return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+  }
+};
 
 // First error recorded in a status word (lowest code), PH_OK if none.
 inline ph_status status_from_bits(unsigned bits) {

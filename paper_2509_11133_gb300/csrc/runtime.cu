@@ -204,20 +204,30 @@ __global__ void __launch_bounds__(SCAN_T) k_scan(const int32_t* in, int32_t* out
   }
 }
 
+size_t scan_state_words(int64_t n) {
+  const int64_t ntiles = n > 0 ? (n + SCAN_TILE - 1) / SCAN_TILE : 1;
+  return (size_t)ntiles + 1;  // tile states, then the tile counter
+}
+
 ph_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* d_total, cudaStream_t s,
-                         unsigned* status, const int64_t* d_len, int64_t len_add) {
+                         unsigned* status, const int64_t* d_len, int64_t len_add, unsigned long long* given) {
   int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (ntiles < 1) ntiles = 1;
-  unsigned long long* state = nullptr;  // ntiles words, then the tile counter
-  cudaError_t e = alloc(&state, (size_t)ntiles + 1, s);
-  if (e != cudaSuccess) return cuda_status(e, "scan alloc");
-  e = cudaMemsetAsync(state, 0, sizeof(unsigned long long) * (ntiles + 1), s);
+  unsigned long long* state = given;  // ntiles words, then the tile counter
+  cudaError_t e = cudaSuccess;
+  if (!state) {
+    e = alloc(&state, (size_t)ntiles + 1, s);
+    if (e != cudaSuccess) return cuda_status(e, "scan alloc");
+    e = cudaMemsetAsync(state, 0, sizeof(unsigned long long) * (ntiles + 1), s);
+  }
   if (e == cudaSuccess) {
+    KernelTimer kt("k_scan", s, 2);
     k_scan<<<(unsigned)ntiles, SCAN_T, 0, s>>>(in, out, n, d_len, len_add, d_total, state,
                                                reinterpret_cast<unsigned*>(state + ntiles), status);
     e = launched();
+    kt.stop();
   }
-  free_async(state, s);
+  if (!given) free_async(state, s);
   return cuda_status(e, "scan");
 }
 
@@ -249,39 +259,73 @@ struct TimedLaunch {
   const char* name;
   cudaEvent_t a, b;
 };
-std::atomic<bool> g_timing{false};
+std::atomic<unsigned> g_timing{0};  // mask of timed categories
 std::mutex g_timing_mu;
 std::vector<TimedLaunch> g_timed;                          // recorded, not yet read
 std::map<std::string, std::pair<double, int64_t>> g_time;  // name -> (ms, launches)
+std::vector<cudaEvent_t> g_event_pool;                     // created once, reused (device of first use)
+
+cudaEvent_t take_event() {
+  {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    if (!g_event_pool.empty()) {
+      cudaEvent_t e = g_event_pool.back();
+      g_event_pool.pop_back();
+      return e;
+    }
+  }
+  cudaEvent_t e = nullptr;
+  return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+}
+
+void give_event(cudaEvent_t e) {  // caller holds g_timing_mu
+  if (e) g_event_pool.push_back(e);
+}
 }  // namespace
 
-KernelTimer::KernelTimer(const char* name, cudaStream_t s) : name_(name), s_(s) {
-  if (!g_timing.load(std::memory_order_relaxed)) return;
+KernelTimer::KernelTimer(const char* name, cudaStream_t s, unsigned category) : name_(name), s_(s) {
+  if (!(g_timing.load(std::memory_order_relaxed) & category)) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
-  if (cudaEventCreate(&a_) != cudaSuccess) { a_ = nullptr; return; }
-  if (cudaEventCreate(&b_) != cudaSuccess || cudaEventRecord(a_, s) != cudaSuccess) {
-    cudaEventDestroy(a_);
-    if (b_) cudaEventDestroy(b_);
+  a_ = take_event();
+  b_ = take_event();
+  if (!a_ || !b_ || cudaEventRecord(a_, s) != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    give_event(a_);
+    give_event(b_);
     a_ = b_ = nullptr;
   }
 }
 
 void KernelTimer::stop() {
   if (!a_) return;
-  if (cudaEventRecord(b_, s_) != cudaSuccess) {
-    cudaEventDestroy(a_);
-    cudaEventDestroy(b_);
-  } else {
-    std::lock_guard<std::mutex> lk(g_timing_mu);
+  const bool ok = cudaEventRecord(b_, s_) == cudaSuccess;
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  if (ok) {
     g_timed.push_back({name_, a_, b_});
+  } else {
+    give_event(a_);
+    give_event(b_);
   }
   a_ = b_ = nullptr;
 }
 }  // namespace ph
 
 extern "C" ph_status ph_timing_enable(int on) {
-  ph::g_timing.store(on != 0);
+  if (on) {  // stock the event pool now, so that timing does not create events between launches
+    constexpr size_t kStock = 4096;
+    std::vector<cudaEvent_t> fresh;
+    {
+      std::lock_guard<std::mutex> lk(ph::g_timing_mu);
+      const size_t have = ph::g_event_pool.size() + 2 * ph::g_timed.size();
+      if (have < kStock) fresh.resize(kStock - have, nullptr);
+    }
+    for (cudaEvent_t& e : fresh)
+      if (cudaEventCreate(&e) != cudaSuccess) return ph::cuda_status(cudaErrorMemoryAllocation, "ph_timing_enable");
+    std::lock_guard<std::mutex> lk(ph::g_timing_mu);
+    for (cudaEvent_t e : fresh) ph::g_event_pool.push_back(e);
+  }
+  ph::g_timing.store(on < 0 ? 0u : (unsigned)on);
   return PH_OK;
 }
 
@@ -305,8 +349,8 @@ extern "C" ph_status ph_kernel_time(const char* kernel, int reset, double* ms, i
     } else if (err == cudaSuccess) {
       err = e;
     }
-    cudaEventDestroy(t.a);
-    cudaEventDestroy(t.b);
+    ph::give_event(t.a);
+    ph::give_event(t.b);
   }
   ph::g_timed.swap(keep);
   auto it = ph::g_time.find(kernel);
