@@ -53,8 +53,8 @@ HBM_PEAK_FALLBACK = 6800.0
 FP64_PEAK_GOPS = 152 * 2 * 2.070
 # FP64 operations per element in k_assemble's formulas (each fma, add, mul or
 # div counted once): condensation kernel Qf 56, load and right-hand side 30,
-# condensed entries 30.
-ASSEMBLE_OPS_PER_TET = 116
+# condensed entries 24 (d_k (Q_km d_m + e_m) for the 10 entries, e_m = d_m/(c|T|)).
+ASSEMBLE_OPS_PER_TET = 110
 # Method-level bytes per element of the numeric phase: coordinates, f and
 # H counted once (136 + 24 nC/nE + 24 nF/nE).
 def assemble_bytes_per_tet(nE, nC, nF):

@@ -115,12 +115,20 @@ __device__ __forceinline__ void assemble_element(int64_t t, const double* __rest
   const double icT = G.rdet * six_over_c;  // 1/(c|T|)
   const double hs = (h[0] + h[1]) + (h[2] + h[3]);
   const double base = icT * hs;
-  // condensed block S[k][m] = d_k d_m (1/(c|T|) + Qf/9), each entry once
+  // condensed block S[k][m] = d_k d_m (1/(c|T|) + Qf/9), each entry once, as
+  // d_k (Q_km d_m + e_m) with d = sigma |F| (sign on the bit pattern) and
+  // e_m = d_m / (c|T|): 4 + 2 per entry FP64 operations
+  double d[4], e4[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    d[k] = neg_if(ar[k], neg[k]);
+    e4[k] = icT * d[k];
+  }
   double S[10];
 #pragma unroll
   for (int k = 0; k < 4; ++k)
 #pragma unroll
-    for (int m = k; m < 4; ++m) S[ut(k, m)] = neg_if((ar[k] * ar[m]) * (icT + Q[ut(k, m)]), neg[k] != neg[m]);
+    for (int m = k; m < 4; ++m) S[ut(k, m)] = d[k] * fma(Q[ut(k, m)], d[m], e4[m]);
   const int4 tp = __ldg(tpos + t);
   const ushort4 tr = __ldg(trel + t);
 #pragma unroll
