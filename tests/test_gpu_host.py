@@ -69,3 +69,15 @@ def test_host_path_checks_counts(ph):
         ph.ph_assemble_host(torch.from_numpy(coord), torch.from_numpy(tet.astype(np.int32)),
                             torch.from_numpy(p.a), 1.0, torch.from_numpy(data["f"]), (nF, L, nnz + 1))
     assert e.value.name == "PH_ERR_ARG"
+
+
+def test_host_path_full_size(ph):
+    """The bench's end-to-end configuration: the lognormal workload (3,359,232
+    tets), pinned buffers, outputs bit-identical to the device entry points."""
+    p = meshgen.problem("lognormal_3m")
+    data, ref, counts = device_path(ph, p)
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    out = ph.ph_assemble_host(pin(p.coord), pin(p.tet.astype(np.int32)), pin(p.a), p.c, pin(data["f"]), counts,
+                              lam=pin(data["lam"]))
+    for k in ("rowptr", "colind", "values", "rhs", "u"):
+        assert torch.equal(out[k], ref[k]), k
