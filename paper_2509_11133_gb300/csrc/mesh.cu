@@ -148,44 +148,11 @@ __global__ void k_face_fill(const int4* __restrict__ tet, int64_t nE, int64_t nC
   }
 }
 
-// Scan entries[j0, j1) for (v0, v1) == (e.x, e.y) (v2 is the bucket's);
-// counts tet and Neumann matches.  Four independent loads per step.
-__device__ __forceinline__ void scan_bucket(const int4* __restrict__ entries, int j0, int j1, int skip, int4 e,
-                                            int64_t ntet, int& nt, int& nn, int& tm) {
-  int j = j0;
-  for (; j + 3 < j1; j += 4) {
-    const int4 k0 = entries[j], k1 = entries[j + 1], k2 = entries[j + 2], k3 = entries[j + 3];
-    const int4 kk[4] = {k0, k1, k2, k3};
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (kk[u].x == e.x && kk[u].y == e.y && j + u != skip) {
-        if (kk[u].w < ntet) { ++nt; tm = kk[u].w; } else { ++nn; }
-      }
-  }
-  for (; j < j1; ++j) {
-    const int4 k = entries[j];
-    if (k.x == e.x && k.y == e.y && j != skip) {
-      if (k.w < ntet) { ++nt; tm = k.w; } else { ++nn; }
-    }
-  }
-}
-
-// 3. match equal keys inside a bucket.  A tet entry compares itself with the
-//    LATER entries of its bucket only and writes both mates of a pair, so each
-//    pair is found once (a second match marks a face in three tets, or a
-//    Neumann triple on an interior face); Neumann entries (boundary only, few)
-//    scan the whole bucket and must match exactly one tet entry.
-__global__ void k_face_match(const int4* __restrict__ entries, int64_t nent, const int32_t* __restrict__ start,
-                             int sub, int64_t nE, int32_t* __restrict__ mate, unsigned* status) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nent || failed(status)) return;
-  const int4 e = entries[i];
-  const int64_t b = bucket_of(make_int3(e.x, e.y, e.z), sub);
-  const int hi = start[b + 1];
-  const int64_t ntet = 4 * nE;
-  int nt = 0, nn = 0, tm = -1;
+// Outcome of one entry's scan: a tet entry records its mate (and its mate's
+// mate) or -2 for a Neumann triple; errors as in k_face_match.
+__device__ __forceinline__ void settle_entry(int4 e, int64_t ntet, int nt, int nn, int tm,
+                                             int32_t* __restrict__ mate, unsigned* status) {
   if (e.w < ntet) {
-    scan_bucket(entries, (int)i + 1, hi, -1, e, ntet, nt, nn, tm);
     if (nt + nn >= 2) ph_flag(status, nn > 0 ? PH_ERR_ARG : PH_ERR_NONMANIFOLD);
     if (nt == 1) {
       mate[e.w] = tm;
@@ -194,10 +161,53 @@ __global__ void k_face_match(const int4* __restrict__ entries, int64_t nent, con
       mate[e.w] = -2;
     }
   } else {
-    scan_bucket(entries, start[b], hi, (int)i, e, ntet, nt, nn, tm);
     if (nt != 1 || nn != 0) ph_flag(status, PH_ERR_ARG);
     else mate[tm] = -2;
   }
+}
+
+__device__ __forceinline__ void count_match(int4 k, int4 e, int64_t ntet, int& nt, int& nn, int& tm) {
+  if (k.x == e.x && k.y == e.y) {
+    if (k.w < ntet) { ++nt; tm = k.w; } else { ++nn; }
+  }
+}
+
+// 3. match equal keys inside a bucket.  A tet entry compares itself with the
+//    LATER entries of its bucket only and writes both mates of a pair, so each
+//    pair is found once (a second match marks a face in three tets, or a
+//    Neumann triple on an interior face); Neumann entries (boundary only, few)
+//    scan the whole bucket and must match exactly one tet entry.  Each thread
+//    takes two entries, i and i + half, and scans their buckets in lockstep:
+//    two independent chains of loads in flight per thread (the kernel is
+//    bound by load latency, not bandwidth).
+__global__ void k_face_match(const int4* __restrict__ entries, int64_t nent, const int32_t* __restrict__ start,
+                             int sub, int64_t nE, int32_t* __restrict__ mate, unsigned* status) {
+  const int64_t half = (nent + 1) >> 1;
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i0 >= half || failed(status)) return;
+  const int64_t i1 = i0 + half;
+  const bool has1 = i1 < nent;
+  const int64_t ntet = 4 * nE;
+  const int4 e0 = entries[i0];
+  const int4 e1 = has1 ? entries[i1] : make_int4(-1, -1, -1, -1);
+  const int64_t b0 = bucket_of(make_int3(e0.x, e0.y, e0.z), sub);
+  const int64_t b1 = has1 ? bucket_of(make_int3(e1.x, e1.y, e1.z), sub) : 0;
+  const int end0 = start[b0 + 1], end1 = has1 ? start[b1 + 1] : 0;
+  // tet entries scan the later entries of their bucket, Neumann entries all of it
+  int j0 = e0.w < ntet ? (int)i0 + 1 : start[b0];
+  int j1 = has1 ? (e1.w < ntet ? (int)i1 + 1 : start[b1]) : 0;
+  int nt0 = 0, nn0 = 0, tm0 = -1, nt1 = 0, nn1 = 0, tm1 = -1;
+  while (j0 < end0 || j1 < end1) {
+    const bool a0 = j0 < end0, a1 = j1 < end1;
+    const int4 k0 = a0 ? entries[j0] : make_int4(-1, -1, -1, -1);
+    const int4 k1 = a1 ? entries[j1] : make_int4(-1, -1, -1, -1);
+    if (a0 && j0 != i0) count_match(k0, e0, ntet, nt0, nn0, tm0);
+    if (a1 && j1 != i1) count_match(k1, e1, ntet, nt1, nn1, tm1);
+    ++j0;
+    ++j1;
+  }
+  settle_entry(e0, ntet, nt0, nn0, tm0, mate, status);
+  if (has1) settle_entry(e1, ntet, nt1, nn1, tm1, mate, status);
 }
 
 __device__ __forceinline__ bool is_first(int m, int s) { return m < 0 || m > s; }
@@ -551,7 +561,7 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
     }
     {
       KernelTimer kt("k_face_match", s, 2);
-      k_face_match<<<grid_for(nent), kThreads, 0, s>>>(entries, nent, start, sub, nE, mate, m->status);
+      k_face_match<<<grid_for((nent + 1) / 2), kThreads, 0, s>>>(entries, nent, start, sub, nE, mate, m->status);
       PH_CU(launched(), "k_face_match");
     }
   }
