@@ -230,30 +230,23 @@ __device__ __forceinline__ int first_rank(int4 m, int s0, int k) {
   return r;
 }
 
-// 5. per tet: face ids, T+/T-, T+'s tuple, kind and non-Neumann flag of the
-//    faces it owns (first occurrences).  Without Neumann faces (mult_iota
-//    given) every face has a multiplier, l(F) = F, so the tet also writes its
-//    slots' multiplier ids and, for the faces it owns, the row length 1 + 3
-//    per tet of the face (7 interior, 4 boundary); k_tet_mult is not needed.
-__global__ void k_face_emit(const int4* __restrict__ tet, int64_t nE, const int4* __restrict__ mate4,
-                            const int32_t* __restrict__ fbase, int4* __restrict__ tface, int2* __restrict__ face_tet,
-                            int32_t* __restrict__ face_vtx, int8_t* __restrict__ face_kind,
-                            int32_t* __restrict__ flag, int32_t* __restrict__ mult_iota, int4* __restrict__ tmult,
-                            int32_t* __restrict__ rowlen, const unsigned* status) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nE || failed(status)) return;
-  int4 v = tet[t];
-  int4 m = mate4[t];
-  int s0 = (int)(4 * t);
+// Outputs of tet t, given its tuple v, mates m, face base fb and, for each
+// face it does not own, its owner's mates om[k] and face base ofb[k].
+__device__ __forceinline__ void emit_tet(int64_t t, int4 v, int4 m, int fb, const int4 om[4], const int ofb[4],
+                                         int64_t nF, int4* __restrict__ tface, int2* __restrict__ face_tet,
+                                         int32_t* __restrict__ face_vtx, int8_t* __restrict__ face_kind,
+                                         int32_t* __restrict__ flag, int32_t* __restrict__ mult_iota,
+                                         int4* __restrict__ tmult, int32_t* __restrict__ rowlen) {
+  const int s0 = (int)(4 * t);
   int out[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    int mk = comp(m, k);
+    const int mk = comp(m, k);
     if (is_first(mk, s0 + k)) {
-      int F = fbase[t] + first_rank(m, s0, k);
+      const int F = fb + first_rank(m, s0, k);
       out[k] = F;
       face_tet[F] = make_int2((int)t, mk >= 0 ? (mk >> 2) : -1);
-      int3 lf = local_face(v, k);
+      const int3 lf = local_face(v, k);
       face_vtx[3 * (int64_t)F] = lf.x;
       face_vtx[3 * (int64_t)F + 1] = lf.y;
       face_vtx[3 * (int64_t)F + 2] = lf.z;
@@ -263,12 +256,11 @@ __global__ void k_face_emit(const int4* __restrict__ tet, int64_t nE, const int4
       if (mult_iota) {                    // none: l(F) = F
         mult_iota[F] = F;
         rowlen[F] = mk >= 0 ? 7 : 4;
-        if (F + 1 == fbase[nE]) rowlen[F + 1] = 0;  // the scan reads one entry past the last row
+        if (F + 1 == nF) rowlen[F + 1] = 0;  // the scan reads one entry past the last row
       }
     } else {
-      int t2 = mk >> 2, k2 = mk & 3;
-      int F = fbase[t2] + first_rank(mate4[t2], 4 * t2, k2);
-      out[k] = (int)((unsigned)F | 0x80000000u);
+      const int t2 = mk >> 2, k2 = mk & 3;
+      out[k] = (int)((unsigned)(ofb[k] + first_rank(om[k], 4 * t2, k2)) | 0x80000000u);
     }
   }
   tface[t] = make_int4(out[0], out[1], out[2], out[3]);
@@ -278,6 +270,52 @@ __global__ void k_face_emit(const int4* __restrict__ tet, int64_t nE, const int4
     for (int k = 0; k < 4; ++k) o[k] = (int)((unsigned)(out[k] & PH_ID_MASK) | (comp(m, k) < 0 ? PH_BND_BIT : 0u));
     tmult[t] = make_int4(o[0], o[1], o[2], o[3]);
   }
+}
+
+// The owner's mates and face base for each face of a tet it does not own.
+__device__ __forceinline__ void load_owners(int64_t t, int4 m, const int4* __restrict__ mate4,
+                                            const int32_t* __restrict__ fbase, int4 om[4], int ofb[4]) {
+  const int s0 = (int)(4 * t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int mk = comp(m, k);
+    if (!is_first(mk, s0 + k)) {
+      om[k] = mate4[mk >> 2];
+      ofb[k] = fbase[mk >> 2];
+    }
+  }
+}
+
+// 5. per tet: face ids, T+/T-, T+'s tuple, kind and non-Neumann flag of the
+//    faces it owns (first occurrences).  Without Neumann faces (mult_iota
+//    given) every face has a multiplier, l(F) = F, so the tet also writes its
+//    slots' multiplier ids and, for the faces it owns, the row length 1 + 3
+//    per tet of the face (7 interior, 4 boundary); k_tet_mult is not needed.
+//    Each thread takes two tets, t and t + half, and issues all their loads
+//    before using any (the kernel is bound by load latency).
+__global__ void k_face_emit(const int4* __restrict__ tet, int64_t nE, const int4* __restrict__ mate4,
+                            const int32_t* __restrict__ fbase, int4* __restrict__ tface, int2* __restrict__ face_tet,
+                            int32_t* __restrict__ face_vtx, int8_t* __restrict__ face_kind,
+                            int32_t* __restrict__ flag, int32_t* __restrict__ mult_iota, int4* __restrict__ tmult,
+                            int32_t* __restrict__ rowlen, const unsigned* status) {
+  const int64_t half = (nE + 1) >> 1;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t0 >= half || failed(status)) return;
+  const int64_t t1 = t0 + half;
+  const bool has1 = t1 < nE;
+  const int nF = fbase[nE];
+  const int4 v0 = tet[t0], m0 = mate4[t0];
+  const int fb0 = fbase[t0];
+  const int4 v1 = has1 ? tet[t1] : make_int4(0, 0, 0, 0);
+  const int4 m1 = has1 ? mate4[t1] : make_int4(-1, -1, -1, -1);
+  const int fb1 = has1 ? fbase[t1] : 0;
+  int4 om0[4], om1[4];
+  int ofb0[4], ofb1[4];
+  load_owners(t0, m0, mate4, fbase, om0, ofb0);
+  if (has1) load_owners(t1, m1, mate4, fbase, om1, ofb1);
+  emit_tet(t0, v0, m0, fb0, om0, ofb0, nF, tface, face_tet, face_vtx, face_kind, flag, mult_iota, tmult, rowlen);
+  if (has1)
+    emit_tet(t1, v1, m1, fb1, om1, ofb1, nF, tface, face_tet, face_vtx, face_kind, flag, mult_iota, tmult, rowlen);
 }
 
 // face area 1/2 |(P_z - P_x) x (P_y - P_x)|
@@ -573,9 +611,9 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   PH_TRY(exclusive_scan(newc, newc, nE + 1, d_tot, s, m->status, nullptr, 0, st2));  // nF -> d_tot[0]
   if (nE > 0) {
     KernelTimer kt("k_face_emit", s, 2);
-    k_face_emit<<<grid_for(nE), kThreads, 0, s>>>(m->tet, nE, reinterpret_cast<int4*>(mate), newc, m->tface,
-                                                  m->face_tet, m->face_vtx, m->face_kind, flag,
-                                                  nN > 0 ? nullptr : m->face_mult, m->tmult, rowlen, m->status);
+    k_face_emit<<<grid_for((nE + 1) / 2), kThreads, 0, s>>>(
+        m->tet, nE, reinterpret_cast<int4*>(mate), newc, m->tface, m->face_tet, m->face_vtx, m->face_kind, flag,
+        nN > 0 ? nullptr : m->face_mult, m->tmult, rowlen, m->status);
     PH_CU(launched(), "k_face_emit");
   }
 
