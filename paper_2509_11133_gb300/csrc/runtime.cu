@@ -75,7 +75,7 @@ void free_async(void* p, cudaStream_t s) {
 // Exclusive scan: reduce tiles -> scan tile sums (one block) -> scan tiles.
 // ---------------------------------------------------------------------------
 constexpr int SCAN_T = 256;
-constexpr int SCAN_I = 8;
+constexpr int SCAN_I = 16;  // a multiple of 4 (16-byte accesses)
 constexpr int SCAN_TILE = SCAN_T * SCAN_I;
 
 template <class T>
@@ -138,8 +138,14 @@ __global__ void __launch_bounds__(SCAN_T) k_scan(const int32_t* in, int32_t* out
   const bool vec = base + SCAN_I <= n && ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   int32_t v[SCAN_I];
   if (vec) {
-    const int4 a = *reinterpret_cast<const int4*>(in + base), b = *reinterpret_cast<const int4*>(in + base + 4);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+#pragma unroll
+    for (int q = 0; q < SCAN_I / 4; ++q) {
+      const int4 a = *reinterpret_cast<const int4*>(in + base + 4 * q);
+      v[4 * q] = a.x;
+      v[4 * q + 1] = a.y;
+      v[4 * q + 2] = a.z;
+      v[4 * q + 3] = a.w;
+    }
   } else {
 #pragma unroll
     for (int i = 0; i < SCAN_I; ++i) v[i] = base + i < n ? in[base + i] : 0;
@@ -195,8 +201,9 @@ __global__ void __launch_bounds__(SCAN_T) k_scan(const int32_t* in, int32_t* out
     run += v[i];
   }
   if (vec) {
-    *reinterpret_cast<int4*>(out + base) = make_int4(o[0], o[1], o[2], o[3]);
-    *reinterpret_cast<int4*>(out + base + 4) = make_int4(o[4], o[5], o[6], o[7]);
+#pragma unroll
+    for (int q = 0; q < SCAN_I / 4; ++q)
+      *reinterpret_cast<int4*>(out + base + 4 * q) = make_int4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
   } else {
 #pragma unroll
     for (int i = 0; i < SCAN_I; ++i)
