@@ -59,11 +59,13 @@ __device__ __forceinline__ int3 neumann_tri(const int32_t* nb, int64_t i) {
   return make_int3(nb[3 * i], nb[3 * i + 1], nb[3 * i + 2]);
 }
 
-// Bucket of a sorted face key (v0 < v1 < v2): the largest vertex and the low
-// `sub` bits of the middle one, so a bucket holds about 2^-sub of the faces
-// whose largest vertex is v2 (short match scans; neighbouring counters).
+// Bucket of a sorted face key (v0 < v1 < v2): the largest vertex and `sub`
+// bits hashed from the other two, so a bucket holds about 2^-sub of the faces
+// whose largest vertex is v2.  Hashing v0 as well as v1 matters: the faces
+// around one edge (v1, v2) share both vertices, and bits of v1 alone leave
+// them all in one bucket (long match scans).
 __device__ __forceinline__ int64_t bucket_of(int3 s, int sub) {
-  return ((int64_t)s.z << sub) | (s.y & ((1 << sub) - 1));
+  return ((int64_t)s.z << sub) | ((s.x ^ s.y) & ((1 << sub) - 1));
 }
 
 // Element geometry of tet t = [P0 P1 P2 P3]: E = rows P_i - P_0 (i = 1..3),
@@ -84,16 +86,18 @@ __device__ __forceinline__ void tet_geom(const double* __restrict__ coord, int4 
   const double g00 = e1x * e1x + e1y * e1y + e1z * e1z, g01 = e1x * e2x + e1y * e2y + e1z * e2z;
   const double g02 = e1x * e3x + e1y * e3y + e1z * e3z, g11 = e2x * e2x + e2y * e2y + e2z * e2z;
   const double g12 = e2x * e3x + e2y * e3y + e2z * e3z, g22 = e3x * e3x + e3y * e3y + e3z * e3z;
-  const double r0 = 0.25 * (g00 + g01 + g02), r1 = 0.25 * (g01 + g11 + g12), r2 = 0.25 * (g02 + g12 + g22);
+  // row sums of G_e; G_e T0^-1 = G_e - (row sum / 4) 1' as one fma per entry
+  // (the quarter is exact, so this rounds like the plain difference)
+  const double r0 = (g00 + g01) + g02, r1 = (g01 + g11) + g12, r2 = (g02 + g12) + g22;
   double2* gg = reinterpret_cast<double2*>(geo + PH_GEO_STRIDE * t);
   gg[0] = make_double2(g00, g01);
   gg[1] = make_double2(g02, g11);
   gg[2] = make_double2(g12, g22);
-  gg[3] = make_double2(g00 - r0, g01 - r0);
-  gg[4] = make_double2(g02 - r0, g01 - r1);
-  gg[5] = make_double2(g11 - r1, g12 - r1);
-  gg[6] = make_double2(g02 - r2, g12 - r2);
-  gg[7] = make_double2(g22 - r2, adet);
+  gg[3] = make_double2(fma(-0.25, r0, g00), fma(-0.25, r0, g01));
+  gg[4] = make_double2(fma(-0.25, r0, g02), fma(-0.25, r1, g01));
+  gg[5] = make_double2(fma(-0.25, r1, g11), fma(-0.25, r1, g12));
+  gg[6] = make_double2(fma(-0.25, r2, g02), fma(-0.25, r2, g12));
+  gg[7] = make_double2(fma(-0.25, r2, g22), adet);
   gg[8] = make_double2(ph::rcp_newton(adet), 0.0);
 }
 
@@ -150,8 +154,8 @@ __global__ void k_face_fill(const int4* __restrict__ tet, int64_t nE, int64_t nC
 
 // Outcome of one entry's scan: a tet entry records its mate (and its mate's
 // mate) or -2 for a Neumann triple; errors as in k_face_match.
-__device__ __forceinline__ void settle_entry(int4 e, int64_t ntet, int nt, int nn, int tm,
-                                             int32_t* __restrict__ mate, unsigned* status) {
+__device__ __forceinline__ void settle_entry(int4 e, int ntet, int nt, int nn, int tm, int32_t* __restrict__ mate,
+                                             unsigned* status) {
   if (e.w < ntet) {
     if (nt + nn >= 2) ph_flag(status, nn > 0 ? PH_ERR_ARG : PH_ERR_NONMANIFOLD);
     if (nt == 1) {
@@ -166,7 +170,9 @@ __device__ __forceinline__ void settle_entry(int4 e, int64_t ntet, int nt, int n
   }
 }
 
-__device__ __forceinline__ void count_match(int4 k, int4 e, int64_t ntet, int& nt, int& nn, int& tm) {
+// k is an entry of e's bucket (same largest vertex) or the sentinel (-1, ...),
+// which equals no entry
+__device__ __forceinline__ void count_match(int4 k, int4 e, int ntet, int& nt, int& nn, int& tm) {
   if (k.x == e.x && k.y == e.y) {
     if (k.w < ntet) { ++nt; tm = k.w; } else { ++nn; }
   }
@@ -176,10 +182,12 @@ __device__ __forceinline__ void count_match(int4 k, int4 e, int64_t ntet, int& n
 //    LATER entries of its bucket only and writes both mates of a pair, so each
 //    pair is found once (a second match marks a face in three tets, or a
 //    Neumann triple on an interior face); Neumann entries (boundary only, few)
-//    scan the whole bucket and must match exactly one tet entry.  Each thread
-//    takes two entries, i and i + half, and scans their buckets in lockstep:
-//    two independent chains of loads in flight per thread (the kernel is
-//    bound by load latency, not bandwidth).
+//    scan the whole bucket, themselves included (one Neumann hit taken off),
+//    and must match exactly one tet entry.  Each thread takes two entries, i
+//    and i + half, and scans their buckets in lockstep: two independent chains
+//    of loads in flight per thread.  The kernel issues instructions at close
+//    to the SM's rate, so the loop carries no more than the loads and
+//    compares; the bucket hash keeps the scans short.
 __global__ void k_face_match(const int4* __restrict__ entries, int64_t nent, const int32_t* __restrict__ start,
                              int sub, int64_t nE, int32_t* __restrict__ mate, unsigned* status) {
   const int64_t half = (nent + 1) >> 1;
@@ -187,22 +195,23 @@ __global__ void k_face_match(const int4* __restrict__ entries, int64_t nent, con
   if (i0 >= half || failed(status)) return;
   const int64_t i1 = i0 + half;
   const bool has1 = i1 < nent;
-  const int64_t ntet = 4 * nE;
+  const int ntet = (int)(4 * nE);  // slots are int32
+  const int4 none = make_int4(-1, -1, -1, -1);
   const int4 e0 = entries[i0];
-  const int4 e1 = has1 ? entries[i1] : make_int4(-1, -1, -1, -1);
+  const int4 e1 = has1 ? entries[i1] : none;
   const int64_t b0 = bucket_of(make_int3(e0.x, e0.y, e0.z), sub);
   const int64_t b1 = has1 ? bucket_of(make_int3(e1.x, e1.y, e1.z), sub) : 0;
   const int end0 = start[b0 + 1], end1 = has1 ? start[b1 + 1] : 0;
   // tet entries scan the later entries of their bucket, Neumann entries all of it
-  int j0 = e0.w < ntet ? (int)i0 + 1 : start[b0];
-  int j1 = has1 ? (e1.w < ntet ? (int)i1 + 1 : start[b1]) : 0;
-  int nt0 = 0, nn0 = 0, tm0 = -1, nt1 = 0, nn1 = 0, tm1 = -1;
+  const bool nm0 = e0.w >= ntet, nm1 = has1 && e1.w >= ntet;
+  int j0 = nm0 ? start[b0] : (int)i0 + 1;
+  int j1 = has1 ? (nm1 ? start[b1] : (int)i1 + 1) : 0;
+  int nt0 = 0, nn0 = nm0 ? -1 : 0, tm0 = -1, nt1 = 0, nn1 = nm1 ? -1 : 0, tm1 = -1;
   while (j0 < end0 || j1 < end1) {
-    const bool a0 = j0 < end0, a1 = j1 < end1;
-    const int4 k0 = a0 ? entries[j0] : make_int4(-1, -1, -1, -1);
-    const int4 k1 = a1 ? entries[j1] : make_int4(-1, -1, -1, -1);
-    if (a0 && j0 != i0) count_match(k0, e0, ntet, nt0, nn0, tm0);
-    if (a1 && j1 != i1) count_match(k1, e1, ntet, nt1, nn1, tm1);
+    const int4 k0 = j0 < end0 ? entries[j0] : none;
+    const int4 k1 = j1 < end1 ? entries[j1] : none;
+    count_match(k0, e0, ntet, nt0, nn0, tm0);
+    count_match(k1, e1, ntet, nt1, nn1, tm1);
     ++j0;
     ++j1;
   }
@@ -511,6 +520,8 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   cudaStream_t s = (cudaStream_t)stream;  // everything runs in order on the caller's stream
   ph_status st = PH_OK;
   // face-key buckets: 4 per largest vertex while the bucket ids stay below 2^31
+  // (finer buckets shorten the match scans but cost more in the scattered
+  // fill and the bucket scan than they save)
   const int sub = nC < ((int64_t)1 << 28) ? 2 : 0;
   const int64_t nb = (nC << sub) + 1;
   const int64_t nent = nFmax;
