@@ -408,6 +408,15 @@ ph_status ph_kernel_time(const char* kernel, int reset, double* ms, int64_t* lau
  */
 ph_status ph_rcp(const double* x, int64_t n, double* y, void* stream);
 
+/*
+ * y[i] = sqrt(x[i])/2 with the device square root the mesh build uses for
+ * the face areas |F| = |(P_z - P_x) x (P_y - P_x)|/2 (Section 4.2, C(T)):
+ * a coupled Newton iteration from a single-precision seed, within one ulp of
+ * the rounded sqrt(x)/2, and 0.5 * sqrt(x) for x outside [2^-960, 2^960).
+ * Device arrays of n doubles; exposed so that its accuracy can be tested.
+ */
+ph_status ph_half_sqrt(const double* x, int64_t n, double* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,7 @@ EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces",
            "ph_launch_count", "ph_solve_pcg_noalloc", "ph_recover_factored", "ph_spmv", "ph_misfit",
            "ph_adjoint_rhs", "ph_adjoint_grad", "ph_batch_create", "ph_batch_destroy", "ph_batch_bind",
            "ph_batch_assemble", "ph_batch_autotune", "ph_batch_set_config", "ph_batch_get_config",
-           "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy", "ph_rcp", "ph_timing_enable",
+           "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy", "ph_rcp", "ph_half_sqrt", "ph_timing_enable",
            "ph_kernel_time", "ph_assemble_host", "ph_schwarz_create", "ph_schwarz_destroy",
            "ph_solve_pcg_schwarz")
 
@@ -93,6 +93,7 @@ def load(path: str | None = None):
         "ph_refined_copy": [P, P, P, P, P],
         "ph_refined_destroy": [P, P],
         "ph_rcp": [P, I64, P, P],
+        "ph_half_sqrt": [P, I64, P, P],
         "ph_timing_enable": [ctypes.c_int],
         "ph_kernel_time": [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(D), ctypes.POINTER(I64)],
         "ph_assemble_host": [P, I64, P, I64, P, I64, I64, I64, I64, P, D, P, P, P, P, P, P, P, P, P, P],
@@ -421,6 +422,14 @@ def ph_rcp(x, stream=None):
     x = x.contiguous()
     y = torch.empty_like(x)
     _check(load().ph_rcp(_ptr(x), x.numel(), _ptr(y), _stream(stream)), "ph_rcp")
+    return y
+
+
+def ph_half_sqrt(x, stream=None):
+    """sqrt(x)/2 with the device square root of the face areas (for testing)."""
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    _check(load().ph_half_sqrt(_ptr(x), x.numel(), _ptr(y), _stream(stream)), "ph_half_sqrt")
     return y
 
 

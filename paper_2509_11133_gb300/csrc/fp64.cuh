@@ -48,4 +48,37 @@ __device__ __forceinline__ double rcp_newton(double x) {
   return fma(y, e, y);
 }
 
+// sqrt(x)/2 (a triangle's area from the squared norm x of its edge cross
+// product) by the coupled Newton iteration for sqrt(q) and 1/(2 sqrt(q)),
+// q = x/4 (Goldschmidt's method, as in Markstein, IBM J. Res. Dev. 34(1),
+// 1990).  The seed y ~ 1/sqrt(q) is the single-precision hardware
+// approximation rsqrt.approx of q's top 23 mantissa bits with q's exponent
+// halved (relative error below 2^-22); then, with g = q y and h = y/2,
+//     r = 1/2 - g h,   g <- g + g r,   h <- h + h r    (error ~1.5 e^2 < 2^-43)
+//     d = q - g g (exact by fma),   g <- g + d h      (error ~e^2, then rounding)
+// so the result is within an ulp of sqrt(x)/2: 6 FP64 operations.  x outside
+// [2^-960, 2^960) -- including zero, subnormal, negative, infinite and NaN x
+// -- takes 0.5 * sqrt(x).
+__device__ __forceinline__ double half_sqrt(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int ex = (int)(hi >> 20);  // biased exponent; >= 2048 when the sign bit is set
+  if (ex < 63 || ex > 1982) return 0.5 * sqrt(x);
+  const double q = __hiloint2double((int)(hi - (2u << 20)), (int)lo);  // x/4, exact
+  const int e = ex - 2 - 1023;                                          // q = m 2^e, m in [1, 2)
+  const int k = e >> 1, p = e & 1;                                      // e = 2k + p
+  const float f = __uint_as_float(((unsigned)(127 + p) << 23) | ((hi & 0x000FFFFFu) << 3) | (lo >> 29));
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(f));  // f = m 2^p in [1, 4), r about 1/sqrt(f)
+  const unsigned rb = __float_as_uint(r);
+  // y = r 2^-k, built on the bit pattern (biased exponent in [500, 1550])
+  const unsigned yhi = ((unsigned)((int)(rb >> 23) - 127 - k + 1023) << 20) | ((rb & 0x007FFFFFu) >> 3);
+  const int ylo = (int)((rb & 0x7u) << 29);
+  double h = __hiloint2double((int)(yhi - (1u << 20)), ylo);  // y/2
+  double g = q * __hiloint2double((int)yhi, ylo);
+  const double t = fma(-g, h, 0.5);
+  g = fma(g, t, g);
+  h = fma(h, t, h);
+  return fma(fma(-g, g, q), h, g);
+}
+
 }  // namespace ph

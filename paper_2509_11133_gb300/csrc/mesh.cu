@@ -336,7 +336,7 @@ __device__ __forceinline__ void face_area(const double* __restrict__ coord, cons
   double u0 = z[0] - x[0], u1 = z[1] - x[1], u2 = z[2] - x[2];
   double v0 = y[0] - x[0], v1 = y[1] - x[1], v2 = y[2] - x[2];
   double cx = u1 * v2 - u2 * v1, cy = u2 * v0 - u0 * v2, cz = u0 * v1 - u1 * v0;
-  area[F] = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+  area[F] = ph::half_sqrt(cx * cx + cy * cy + cz * cz);
 }
 
 // Neumann faces get no multiplier.  Face counts are read on the device

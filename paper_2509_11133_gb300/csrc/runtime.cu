@@ -372,6 +372,11 @@ __global__ void k_rcp(const double* __restrict__ x, int64_t n, double* __restric
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = ph::rcp_newton(x[i]);
 }
+
+__global__ void k_half_sqrt(const double* __restrict__ x, int64_t n, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = ph::half_sqrt(x[i]);
+}
 }  // namespace
 
 extern "C" ph_status ph_rcp(const double* x, int64_t n, double* y, void* stream) {
@@ -379,4 +384,11 @@ extern "C" ph_status ph_rcp(const double* x, int64_t n, double* y, void* stream)
   if (n == 0) return PH_OK;
   k_rcp<<<ph::grid_for(n), ph::kThreads, 0, (cudaStream_t)stream>>>(x, n, y);
   return ph::cuda_status(ph::launched(), "k_rcp");
+}
+
+extern "C" ph_status ph_half_sqrt(const double* x, int64_t n, double* y, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return PH_ERR_ARG;
+  if (n == 0) return PH_OK;
+  k_half_sqrt<<<ph::grid_for(n), ph::kThreads, 0, (cudaStream_t)stream>>>(x, n, y);
+  return ph::cuda_status(ph::launched(), "k_half_sqrt");
 }
