@@ -387,8 +387,8 @@ ph_status ph_assemble_host(const double* coord, int64_t nC, const int32_t* tet, 
  * Kernel timing, off by default.  `on` is a mask: bit 0 times k_assemble,
  * zero_values (the clearing of values and rhs), k_recover and
  * k_recover_factored; bit 1 the mesh-build kernels
- * (k_face_count, k_face_fill, k_face_match, k_new_count, k_face_emit,
- * k_row_fill) and the scans (k_scan); 0 switches timing off.  A timed launch
+ * (k_face_count, k_face_fill, k_face_match, k_face_emit, k_row_fill) and
+ * the scans (k_scan); 0 switches timing off.  A timed launch
  * is bracketed by a pair of CUDA events on the stream it runs on (not while
  * that stream is being captured into a graph); the events come from a pool
  * stocked when timing is switched on.  Timing the mesh build adds host work

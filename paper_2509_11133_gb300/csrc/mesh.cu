@@ -219,23 +219,15 @@ __global__ void k_face_match(const int4* __restrict__ entries, int64_t nent, con
   if (has1) settle_entry(e1, ntet, nt1, nn1, tm1, mate, status);
 }
 
-__device__ __forceinline__ bool is_first(int m, int s) { return m < 0 || m > s; }
-
-// 4. number of faces whose first occurrence is in tet t
-__global__ void k_new_count(const int4* __restrict__ mate4, int64_t nE, int32_t* __restrict__ newc,
-                            const unsigned* status) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nE || failed(status)) return;
-  int4 m = mate4[t];
-  int s = (int)(4 * t);
-  newc[t] = is_first(m.x, s) + is_first(m.y, s + 1) + is_first(m.z, s + 2) + is_first(m.w, s + 3);
-}
+// 4. face bases: an exclusive scan of the number of first occurrences per tet,
+//    which the scan itself counts from the mates (exclusive_scan's `mates`).
+using ph::first_occurrence;
 
 __device__ __forceinline__ int first_rank(int4 m, int s0, int k) {
   int r = 0;
-  if (k > 0) r += is_first(m.x, s0);
-  if (k > 1) r += is_first(m.y, s0 + 1);
-  if (k > 2) r += is_first(m.z, s0 + 2);
+  if (k > 0) r += first_occurrence(m.x, s0);
+  if (k > 1) r += first_occurrence(m.y, s0 + 1);
+  if (k > 2) r += first_occurrence(m.z, s0 + 2);
   return r;
 }
 
@@ -251,7 +243,7 @@ __device__ __forceinline__ void emit_tet(int64_t t, int4 v, int4 m, int fb, cons
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int mk = comp(m, k);
-    if (is_first(mk, s0 + k)) {
+    if (first_occurrence(mk, s0 + k)) {
       const int F = fb + first_rank(m, s0, k);
       out[k] = F;
       face_tet[F] = make_int2((int)t, mk >= 0 ? (mk >> 2) : -1);
@@ -288,7 +280,7 @@ __device__ __forceinline__ void load_owners(int64_t t, int4 m, const int4* __res
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int mk = comp(m, k);
-    if (!is_first(mk, s0 + k)) {
+    if (!first_occurrence(mk, s0 + k)) {
       om[k] = mate4[mk >> 2];
       ofb[k] = fbase[mk >> 2];
     }
@@ -541,7 +533,7 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   const size_t o_farea = mc.take<double>(nFmax), o_rowptr = mc.take<int32_t>(nFmax + 1);
   const size_t o_colind = mc.take<int32_t>(nnzmax), o_rowdiag = mc.take<int32_t>(nFmax);
   // scratch: zeroed part first
-  const size_t o_tot = sc.take<int64_t>(3), o_cnt = sc.take<int32_t>(nb), o_newc = sc.take<int32_t>(nE + 1);
+  const size_t o_tot = sc.take<int64_t>(3), o_cnt = sc.take<int32_t>(nb);
   const size_t o_s1 = sc.take<unsigned long long>(scan_state_words(nb));
   const size_t o_s2 = sc.take<unsigned long long>(scan_state_words(nE + 1));
   const size_t o_s3 = sc.take<unsigned long long>(scan_state_words(nFmax + 1));
@@ -550,6 +542,7 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   const size_t o_flag = sc.take<int32_t>(nN > 0 ? nFmax + 1 : 0);
   const size_t zero_bytes = sc.bytes;
   const size_t o_start = sc.take<int32_t>(nb), o_entries = sc.take<int4>(nent), o_mate = sc.take<int32_t>(4 * nE);
+  const size_t o_newc = sc.take<int32_t>(nE + 1);
   const size_t o_rowlen2 = sc.take<int32_t>(nN > 0 || nE == 0 ? 0 : nFmax + 1);
   void* scratch = nullptr;
   PH_CU(cudaGetDevice(&m->device), "cudaGetDevice");
@@ -614,12 +607,9 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
       PH_CU(launched(), "k_face_match");
     }
   }
-  if (nE > 0) {
-    KernelTimer kt("k_new_count", s, 2);
-    k_new_count<<<grid_for(nE), kThreads, 0, s>>>(reinterpret_cast<int4*>(mate), nE, newc, m->status);
-    PH_CU(launched(), "k_new_count");
-  }
-  PH_TRY(exclusive_scan(newc, newc, nE + 1, d_tot, s, m->status, nullptr, 0, st2));  // nF -> d_tot[0]
+  // face bases: the scan counts each tet's first occurrences from the mates
+  PH_TRY(exclusive_scan(nullptr, newc, nE + 1, d_tot, s, m->status, nullptr, 0, st2,
+                        reinterpret_cast<const int4*>(mate), nE));  // nF -> d_tot[0]
   if (nE > 0) {
     KernelTimer kt("k_face_emit", s, 2);
     k_face_emit<<<grid_for((nE + 1) / 2), kThreads, 0, s>>>(

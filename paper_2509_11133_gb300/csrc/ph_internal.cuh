@@ -86,9 +86,21 @@ void free_async(void* p, cudaStream_t s);
 // PH_ERR_TIMEOUT in *status (if given) instead of hanging.
 // `state` (optional): a zeroed workspace of scan_state_words(n) words; without
 // it the scan allocates and clears its own.
+// `mates` (optional, replaces `in`): the face mates of nmates tets (mate slot
+// of each local face, see first_occurrence); value i is the number of faces
+// whose first occurrence is in tet i (0 for i >= nmates), so the scan numbers
+// the faces without a separate counting pass.
 ph_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* d_total, cudaStream_t s,
                          unsigned* status = nullptr, const int64_t* d_len = nullptr, int64_t len_add = 0,
-                         unsigned long long* state = nullptr);
+                         unsigned long long* state = nullptr, const int4* mates = nullptr, int64_t nmates = 0);
+
+// Local face slot s = 4t + k is the first occurrence of its face when its mate
+// slot m is a boundary mark (m < 0) or a later slot.
+__device__ __forceinline__ bool first_occurrence(int m, int s) { return m < 0 || m > s; }
+__device__ __forceinline__ int first_occurrences(int4 m, int s0) {
+  return first_occurrence(m.x, s0) + first_occurrence(m.y, s0 + 1) + first_occurrence(m.z, s0 + 2) +
+         first_occurrence(m.w, s0 + 3);
+}
 size_t scan_state_words(int64_t n);
 
 // Sub-arrays of one allocation, each starting on a 256-byte boundary.

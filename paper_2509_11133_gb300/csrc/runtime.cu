@@ -125,7 +125,8 @@ constexpr int kScanSpinLimit = 1 << 20;  // unready polls before giving up (>= 3
 __global__ void __launch_bounds__(SCAN_T) k_scan(const int32_t* in, int32_t* out, int64_t nmax,
                                                   const int64_t* __restrict__ d_len, int64_t len_add,
                                                   int64_t* __restrict__ d_total, unsigned long long* state,
-                                                  unsigned* counter, unsigned* status) {
+                                                  unsigned* counter, unsigned* status,
+                                                  const int4* __restrict__ mates, int64_t nmates) {
   __shared__ unsigned s_tile;
   __shared__ int64_t s_prefix;
   if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
@@ -137,7 +138,13 @@ __global__ void __launch_bounds__(SCAN_T) k_scan(const int32_t* in, int32_t* out
   const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_I;
   const bool vec = base + SCAN_I <= n && ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   int32_t v[SCAN_I];
-  if (vec) {
+  if (mates) {  // first occurrences per tet, from the face mates
+#pragma unroll
+    for (int i = 0; i < SCAN_I; ++i) {
+      const int64_t t = base + i;
+      v[i] = t < nmates && t < n ? first_occurrences(mates[t], (int)(4 * t)) : 0;
+    }
+  } else if (vec) {
 #pragma unroll
     for (int q = 0; q < SCAN_I / 4; ++q) {
       const int4 a = *reinterpret_cast<const int4*>(in + base + 4 * q);
@@ -217,7 +224,8 @@ size_t scan_state_words(int64_t n) {
 }
 
 ph_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* d_total, cudaStream_t s,
-                         unsigned* status, const int64_t* d_len, int64_t len_add, unsigned long long* given) {
+                         unsigned* status, const int64_t* d_len, int64_t len_add, unsigned long long* given,
+                         const int4* mates, int64_t nmates) {
   int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (ntiles < 1) ntiles = 1;
   unsigned long long* state = given;  // ntiles words, then the tile counter
@@ -230,7 +238,8 @@ ph_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* d_
   if (e == cudaSuccess) {
     KernelTimer kt("k_scan", s, 2);
     k_scan<<<(unsigned)ntiles, SCAN_T, 0, s>>>(in, out, n, d_len, len_add, d_total, state,
-                                               reinterpret_cast<unsigned*>(state + ntiles), status);
+                                               reinterpret_cast<unsigned*>(state + ntiles), status, mates,
+                                               nmates);
     e = launched();
     kt.stop();
   }
