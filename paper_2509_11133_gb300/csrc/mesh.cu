@@ -293,7 +293,7 @@ __device__ __forceinline__ void load_owners(int64_t t, int4 m, const int4* __res
 //    slots' multiplier ids and, for the faces it owns, the row length 1 + 3
 //    per tet of the face (7 interior, 4 boundary); k_tet_mult is not needed.
 //    Each thread takes two tets, t and t + half, and issues all their loads
-//    before using any (the kernel is bound by load latency).
+//    before using any (its warps mostly wait on loads).
 __global__ void k_face_emit(const int4* __restrict__ tet, int64_t nE, const int4* __restrict__ mate4,
                             const int32_t* __restrict__ fbase, int4* __restrict__ tface, int2* __restrict__ face_tet,
                             int32_t* __restrict__ face_vtx, int8_t* __restrict__ face_kind,
