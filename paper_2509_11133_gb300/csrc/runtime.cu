@@ -138,11 +138,24 @@ __global__ void __launch_bounds__(SCAN_T) k_scan(const int32_t* in, int32_t* out
   const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_I;
   const bool vec = base + SCAN_I <= n && ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   int32_t v[SCAN_I];
-  if (mates) {  // first occurrences per tet, from the face mates
+  if (mates) {
+    // first occurrences per tet, from the face mates: the block loads the
+    // tile's mates with consecutive threads on consecutive tets (coalesced),
+    // counts them, and hands each thread its SCAN_I consecutive counts through
+    // shared memory (one pad word per 32, so both passes are free of bank
+    // conflicts)
+    __shared__ int32_t s_cnt[SCAN_TILE + SCAN_TILE / 32];
+#pragma unroll
+    for (int q = 0; q < SCAN_I; ++q) {
+      const int j = q * SCAN_T + threadIdx.x;
+      const int64_t t = tile * SCAN_TILE + j;
+      s_cnt[j + (j >> 5)] = t < nmates && t < n ? first_occurrences(mates[t], (int)(4 * t)) : 0;
+    }
+    __syncthreads();
 #pragma unroll
     for (int i = 0; i < SCAN_I; ++i) {
-      const int64_t t = base + i;
-      v[i] = t < nmates && t < n ? first_occurrences(mates[t], (int)(4 * t)) : 0;
+      const int j = threadIdx.x * SCAN_I + i;
+      v[i] = s_cnt[j + (j >> 5)];
     }
   } else if (vec) {
 #pragma unroll
