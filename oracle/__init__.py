@@ -15,9 +15,13 @@ Functions and the passage each one follows:
   tet_local          Eqs. K(T), M(T), C(T); Eq. schur; Algorithm 1 first loop
   tet_recover        Algorithm 1 second loop, one element
   tet_matrices       Eqs. K(T), M(T), C(T) and the load rule of Section 4.3
-  assemble           Algorithm 1 assembly + b_D (Section 4.3)
+  assemble           Algorithm 1 assembly + b_D (Section 4.3); its element
+                     loop may run on several host threads (same bits)
   solve              Eq. schur, S Lambda = rhs (a library sparse/dense solve)
-  recover            Algorithm 1 second loop
+  residual, solve_refined
+                     the same solve refined to fp64 accuracy (residual in
+                     binary128)
+  recover            Algorithm 1 second loop (host threads as assemble)
   element_blocks     Eq. VectorForm blocks (monolithic check)
   misfit, monolithic, adjoint_gradient
                      gradient of J = 1/2 sum_T e' M(T) e with respect to
@@ -53,7 +57,7 @@ def build(force: bool = False) -> str:
     """Compile ph_oracle.c into libph_oracle.so next to it (plain gcc)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-fopenmp", "-shared", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -72,8 +76,12 @@ def _configure(L):
     L.or_recover.argtypes = [I64, P, P, P, P, P, P, D, P, P, P, P]
     L.or_element_blocks.argtypes = [I64, P, P, P, P, P, D, P, P, P, P, P]
     L.or_tet_recover.argtypes = [P, D, D, P, P, P, P, P, P]
+    L.or_residual.argtypes = [I64, P, P, P, P, P, P]
+    L.or_assemble_mt.argtypes = L.or_assemble.argtypes + [ctypes.c_int]
+    L.or_recover_mt.argtypes = L.or_recover.argtypes + [ctypes.c_int]
     for f in ("or_faces", "or_multipliers", "or_csr_pattern", "or_face_centroids", "or_tet_local",
-              "or_tet_matrices", "or_assemble", "or_recover", "or_element_blocks", "or_tet_recover"):
+              "or_tet_matrices", "or_assemble", "or_recover", "or_element_blocks", "or_tet_recover",
+              "or_assemble_mt", "or_recover_mt", "or_residual"):
         getattr(L, f).restype = ctypes.c_int
     return L
 
@@ -204,8 +212,15 @@ def tet_matrices(P, f4=(0, 0, 0, 0), sigma4=(1, 1, 1, 1)):
             "vol": vol.value, "B": B}
 
 
-def assemble(coord, tet, fc, csr, a, c, f_face, uD_face=None, gN_face=None):
-    """fc: output of faces(); csr: dict with face_mult, L, rowptr, colind."""
+def threads() -> int:
+    """Host threads the element loops use by default (every core)."""
+    return max(1, os.cpu_count() or 1)
+
+
+def assemble(coord, tet, fc, csr, a, c, f_face, uD_face=None, gN_face=None, nthreads=None):
+    """fc: output of faces(); csr: dict with face_mult, L, rowptr, colind.
+    nthreads = 1 runs the plain element loop; more threads share out the
+    element computations (bit-identical result, see or_assemble_mt)."""
     coord = _c(coord, np.float64)
     tet = _c(tet, np.int32)
     nE = tet.shape[0]
@@ -218,23 +233,32 @@ def assemble(coord, tet, fc, csr, a, c, f_face, uD_face=None, gN_face=None):
     f_face = _c(f_face, np.float64)
     uD = None if uD_face is None else _c(uD_face, np.float64)
     gN = None if gN_face is None else _c(gN_face, np.float64)
-    _check(_lib().or_assemble(nE, _p(coord), _p(tet), _p(_c(fc["tet_face"], np.int32)), fc["nF"],
-                              _p(_c(fc["face_kind"], np.int8)), _p(_c(csr["face_mult"], np.int32)),
-                              _p(_c(fc["face_vtx"], np.int32)), L, _p(rowptr), _p(colind), _p(a), float(c),
-                              _p(f_face), _p(uD), _p(gN), _p(values), _p(rhs), _p(rhs_abs)), "assemble")
+    nt = threads() if nthreads is None else int(nthreads)
+    args = [nE, _p(coord), _p(tet), _p(_c(fc["tet_face"], np.int32)), fc["nF"], _p(_c(fc["face_kind"], np.int8)),
+            _p(_c(csr["face_mult"], np.int32)), _p(_c(fc["face_vtx"], np.int32)), L, _p(rowptr), _p(colind), _p(a),
+            float(c), _p(f_face), _p(uD), _p(gN), _p(values), _p(rhs), _p(rhs_abs)]
+    if nt <= 1:
+        _check(_lib().or_assemble(*args), "assemble")
+    else:
+        _check(_lib().or_assemble_mt(*args, nt), "assemble")
     return values[:colind.size], rhs[:L], rhs_abs[:L]
 
 
-def recover(coord, tet, fc, face_mult, a, c, f_face, lam, gN_face=None):
+def recover(coord, tet, fc, face_mult, a, c, f_face, lam, gN_face=None, nthreads=None):
     coord = _c(coord, np.float64)
     tet = _c(tet, np.int32)
     nE = tet.shape[0]
     U = np.zeros((max(nE, 1), 4))
     gN = None if gN_face is None else _c(gN_face, np.float64)
     lam = _c(lam if len(lam) else np.zeros(1), np.float64)
-    _check(_lib().or_recover(nE, _p(coord), _p(tet), _p(_c(fc["tet_face"], np.int32)),
-                             _p(_c(fc["face_kind"], np.int8)), _p(_c(face_mult, np.int32)), _p(_c(a, np.float64)),
-                             float(c), _p(_c(f_face, np.float64)), _p(gN), _p(lam), _p(U)), "recover")
+    args = [nE, _p(coord), _p(tet), _p(_c(fc["tet_face"], np.int32)), _p(_c(fc["face_kind"], np.int8)),
+            _p(_c(face_mult, np.int32)), _p(_c(a, np.float64)), float(c), _p(_c(f_face, np.float64)), _p(gN),
+            _p(lam), _p(U)]
+    nt = threads() if nthreads is None else int(nthreads)
+    if nt <= 1:
+        _check(_lib().or_recover(*args), "recover")
+    else:
+        _check(_lib().or_recover_mt(*args, nt), "recover")
     return U[:nE]
 
 
@@ -265,6 +289,68 @@ def solve(rowptr, colind, values, rhs):
     import scipy.sparse.linalg as spla
     H = sp.csr_matrix((values, colind, rowptr), shape=(L, L)).tocsc()
     return spla.spsolve(H, rhs)
+
+
+def residual(rowptr, colind, values, x, b):
+    """b - H x with the row sums formed in binary128 (see or_residual)."""
+    n = b.size
+    r = np.zeros(max(n, 1))
+    rp, ci = _c(rowptr, np.int32), _c(colind, np.int32)
+    _check(_lib().or_residual(n, _p(rp), _p(ci), _p(_c(values, np.float64)), _p(_c(x, np.float64)),
+                              _p(_c(b, np.float64)), _p(r)), "residual")
+    return r[:n]
+
+
+def solve_refined(rowptr, colind, values, rhs, max_steps=20):
+    """S Lambda = rhs solved to fp64 accuracy: a library LU solve, then
+    iterative refinement (Wilkinson) with the residual in binary128, until
+    the correction is below 2^-53 of the solution.  The error of a plain fp64
+    solve is ~cond(H) eps; this one is ~eps for cond(H) eps << 1.
+    Returns (Lambda, refinement steps, last relative correction)."""
+    L = rhs.size
+    if L == 0:
+        return np.zeros(0), 0, 0.0
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    H = sp.csr_matrix((values, colind, rowptr), shape=(L, L)).tocsc()
+    lu = spla.splu(H)
+    x = lu.solve(np.asarray(rhs, np.float64))
+    corr = np.inf
+    for step in range(1, max_steps + 1):
+        d = lu.solve(residual(rowptr, colind, values, x, rhs))
+        x = x + d
+        corr = np.linalg.norm(d) / max(np.linalg.norm(x), 1e-300)
+        if corr <= 2.0 ** -53:
+            return x, step, corr
+    return x, max_steps, corr
+
+
+def ulp_sensitivity(rowptr, colind, values, rhs, trials=3, seed=0):
+    """Intrinsic sensitivity of the solved face values to the last bit of the
+    assembled system: the largest normwise relative change of Lambda (both
+    solves refined to fp64 accuracy) when every entry of H -- keeping H
+    symmetric -- and of rhs moves by one ulp in a seeded random direction.
+    Two correct fp64 assemblies differ by about that much in each entry, so
+    no fp64 path can promise solved values closer than this."""
+    import scipy.sparse as sp
+    L = rhs.size
+    x, _, _ = solve_refined(rowptr, colind, values, rhs)
+    H = sp.csr_matrix((values, colind, rowptr), shape=(L, L)).tocoo()
+    i, j, v = H.row.astype(np.int64), H.col.astype(np.int64), H.data
+    lo, hi = np.minimum(i, j), np.maximum(i, j)
+    worst = 0.0
+    for t in range(trials):
+        rng = np.random.Generator(np.random.PCG64(seed + t))
+        # direction of entry (i, j) = that of (min, max): a symmetric perturbation
+        key = np.unique(lo * L + hi, return_inverse=True)[1]
+        up = rng.random(key.max() + 1)[key] < 0.5
+        v2 = np.where(up, np.nextafter(v, np.inf), np.nextafter(v, -np.inf))
+        H2 = sp.csr_matrix((v2, (i, j)), shape=(L, L))
+        H2.sort_indices()
+        b2 = np.where(rng.random(L) < 0.5, np.nextafter(rhs, np.inf), np.nextafter(rhs, -np.inf))
+        x2, _, _ = solve_refined(H2.indptr.astype(np.int32), H2.indices.astype(np.int32), H2.data, b2)
+        worst = max(worst, float(np.linalg.norm(x2 - x) / np.linalg.norm(x)))
+    return worst
 
 
 def pipeline(coord, tet, a, c, f_fn, uD_fn=None, gN_fn=None, neumann=None, do_solve=True):

@@ -435,6 +435,58 @@ static int64_t find_col(const int32_t* rowptr, const int32_t* colind, int32_t ro
   return -1;
 }
 
+static int add_dirichlet(int64_t nF, const double* coord, const int8_t* face_kind, const int32_t* face_mult,
+                         const int32_t* face_vtx, const double* uD_face, double* rhs, double* rhs_abs);
+
+/* H[l(F_k), l(F_m)] += S[k][m] and rhs[l(F_k)] += g[k] for the non-Neumann
+ * local faces of one element (P_T' S(T) P_T in Algorithm 1's assembly). */
+static int scatter_element(const int32_t mult[4], const double S[16], const double g[4], const int32_t* rowptr,
+                           const int32_t* colind, double* values, double* rhs, double* rhs_abs) {
+  for (int k = 0; k < 4; ++k) {
+    if (mult[k] < 0) continue;
+    for (int m = 0; m < 4; ++m) {
+      if (mult[m] < 0) continue;
+      int64_t pos = find_col(rowptr, colind, mult[k], mult[m]);
+      if (pos < 0) return OR_ERR_ARG;
+      values[pos] += S[4 * k + m];
+    }
+    rhs[mult[k]] += g[k];
+    rhs_abs[mult[k]] += fabs(g[k]);
+  }
+  return OR_OK;
+}
+
+/* Inputs of element t: vertices, and per local face sigma, kind, multiplier,
+ * f and g. */
+static void element_inputs(int64_t t, const double* coord, const int32_t* tet, const int32_t* tet_face,
+                           const int8_t* face_kind, const int32_t* face_mult, const double* f_face,
+                           const double* gN_face, double P[4][3], int32_t sig[4], int32_t kind[4],
+                           int32_t mult[4], double f4[4], double g4[4]) {
+  gather_tet(coord, tet, t, P);
+  for (int k = 0; k < 4; ++k) {
+    int32_t tf = tet_face[4 * t + k];
+    int32_t F = tf & 0x7fffffff;
+    sig[k] = (tf < 0) ? -1 : 1;
+    kind[k] = face_kind[F];
+    mult[k] = face_mult[F];
+    f4[k] = f_face[F];
+    g4[k] = gN_face ? gN_face[F] : 0.0;
+  }
+}
+
+/* S(T) and g(T) of element t (Eq. schur, Algorithm 1 first loop) and the
+ * multiplier ids of its faces. */
+static int condense_element(int64_t t, const double* coord, const int32_t* tet, const int32_t* tet_face,
+                            const int8_t* face_kind, const int32_t* face_mult, const double* a, double c,
+                            const double* f_face, const double* gN_face, int32_t mult[4], double S[16],
+                            double g[4]) {
+  double P[4][3], f4[4], g4[4];
+  int32_t sig[4], kind[4];
+  element_inputs(t, coord, tet, tet_face, face_kind, face_mult, f_face, gN_face, P, sig, kind, mult, f4, g4);
+  if (!(a[t] > 0) || !isfinite(a[t])) return OR_ERR_ARG;
+  return or_tet_local(&P[0][0], a[t], c, f4, sig, kind, g4, S, g);
+}
+
 /* Global condensed system H Lambda = rhs with H = sum_T P_T' S(T) P_T and
  * rhs = sum_T P_T' g(T) + b_D, b_D(F) = |F| u_D(Ct_F) on Dirichlet faces
  * (Section 4.3).  values is aligned with (rowptr, colind).  rhs_abs receives the
@@ -450,33 +502,62 @@ int or_assemble(int64_t nE, const double* coord, const int32_t* tet, const int32
   for (int64_t i = 0; i < L; ++i) { rhs[i] = 0; rhs_abs[i] = 0; }
   if (!(c > 0) || !isfinite(c)) return OR_ERR_ARG;
   for (int64_t t = 0; t < nE; ++t) {
-    double P[4][3], f4[4], g4[4], S[16], g[4];
-    int32_t sig[4], kind[4], mult[4];
-    gather_tet(coord, tet, t, P);
-    for (int k = 0; k < 4; ++k) {
-      int32_t tf = tet_face[4 * t + k];
-      int32_t F = tf & 0x7fffffff;
-      sig[k] = (tf < 0) ? -1 : 1;
-      kind[k] = face_kind[F];
-      mult[k] = face_mult[F];
-      f4[k] = f_face[F];
-      g4[k] = gN_face ? gN_face[F] : 0.0;
-    }
-    if (!(a[t] > 0) || !isfinite(a[t])) return OR_ERR_ARG;
-    int st = or_tet_local(&P[0][0], a[t], c, f4, sig, kind, g4, S, g);
+    double S[16], g[4];
+    int32_t mult[4];
+    int st = condense_element(t, coord, tet, tet_face, face_kind, face_mult, a, c, f_face, gN_face, mult, S, g);
     if (st != OR_OK) return st;
-    for (int k = 0; k < 4; ++k) {
-      if (mult[k] < 0) continue;
-      for (int m = 0; m < 4; ++m) {
-        if (mult[m] < 0) continue;
-        int64_t pos = find_col(rowptr, colind, mult[k], mult[m]);
-        if (pos < 0) return OR_ERR_ARG;
-        values[pos] += S[4 * k + m];
-      }
-      rhs[mult[k]] += g[k];
-      rhs_abs[mult[k]] += fabs(g[k]);
+    st = scatter_element(mult, S, g, rowptr, colind, values, rhs, rhs_abs);
+    if (st != OR_OK) return st;
+  }
+  return add_dirichlet(nF, coord, face_kind, face_mult, face_vtx, uD_face, rhs, rhs_abs);
+}
+
+/* Element chunk of the multi-threaded loops below. */
+#define OR_CHUNK ((int64_t)1 << 18)
+
+/* or_assemble with the element computations shared out across `nthreads`
+ * threads (OpenMP): each element's S(T), g(T) go to a buffer, and one thread
+ * then scatters them in element order, so values and rhs are bit-identical to
+ * or_assemble's.  The first error in element order is returned, as there. */
+int or_assemble_mt(int64_t nE, const double* coord, const int32_t* tet, const int32_t* tet_face,
+                   int64_t nF, const int8_t* face_kind, const int32_t* face_mult,
+                   const int32_t* face_vtx, int64_t L, const int32_t* rowptr, const int32_t* colind,
+                   const double* a, double c, const double* f_face, const double* uD_face,
+                   const double* gN_face, double* values, double* rhs, double* rhs_abs, int nthreads) {
+  int64_t nnz = rowptr[L];
+  for (int64_t i = 0; i < nnz; ++i) values[i] = 0;
+  for (int64_t i = 0; i < L; ++i) { rhs[i] = 0; rhs_abs[i] = 0; }
+  if (!(c > 0) || !isfinite(c)) return OR_ERR_ARG;
+  const int64_t cap = nE < OR_CHUNK ? (nE > 0 ? nE : 1) : OR_CHUNK;
+  double* S = (double*)malloc(sizeof(double) * 16 * (size_t)cap);
+  double* g = (double*)malloc(sizeof(double) * 4 * (size_t)cap);
+  int32_t* mult = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)cap);
+  int* st = (int*)malloc(sizeof(int) * (size_t)cap);
+  if (!S || !g || !mult || !st) {
+    free(S); free(g); free(mult); free(st);
+    return OR_ERR_NOMEM;
+  }
+  int status = OR_OK;
+  for (int64_t t0 = 0; t0 < nE && status == OR_OK; t0 += OR_CHUNK) {
+    const int64_t n = nE - t0 < OR_CHUNK ? nE - t0 : OR_CHUNK;
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
+    for (int64_t i = 0; i < n; ++i)
+      st[i] = condense_element(t0 + i, coord, tet, tet_face, face_kind, face_mult, a, c, f_face, gN_face,
+                               mult + 4 * i, S + 16 * i, g + 4 * i);
+    for (int64_t i = 0; i < n && status == OR_OK; ++i) {
+      status = st[i];
+      if (status == OR_OK)
+        status = scatter_element(mult + 4 * i, S + 16 * i, g + 4 * i, rowptr, colind, values, rhs, rhs_abs);
     }
   }
+  free(S); free(g); free(mult); free(st);
+  if (status != OR_OK) return status;
+  return add_dirichlet(nF, coord, face_kind, face_mult, face_vtx, uD_face, rhs, rhs_abs);
+}
+
+/* b_D(F) = |F| u_D(Ct_F), added once per Dirichlet face (Section 4.3). */
+static int add_dirichlet(int64_t nF, const double* coord, const int8_t* face_kind, const int32_t* face_mult,
+                         const int32_t* face_vtx, const double* uD_face, double* rhs, double* rhs_abs) {
   if (uD_face) {
     for (int64_t F = 0; F < nF; ++F) {
       if (face_kind[F] != KIND_DIRICHLET) continue;
@@ -494,6 +575,31 @@ int or_assemble(int64_t nE, const double* coord, const int32_t* tet, const int32
   return OR_OK;
 }
 
+/* Recovery of element t: U(T) = A^-1 (B + C' Lambda_T) into U[4t..4t+3]. */
+static int recover_element(int64_t t, const double* coord, const int32_t* tet, const int32_t* tet_face,
+                           const int8_t* face_kind, const int32_t* face_mult, const double* a, double c,
+                           const double* f_face, const double* gN_face, const double* lambda, double* U) {
+  double P[4][3], f4[4], g4[4];
+  int32_t sig[4], kind[4], mult[4];
+  qf lam[4];
+  element_inputs(t, coord, tet, tet_face, face_kind, face_mult, f_face, gN_face, P, sig, kind, mult, f4, g4);
+  for (int k = 0; k < 4; ++k) lam[k] = mult[k] >= 0 ? (qf)lambda[mult[k]] : 0;
+  if (!(a[t] > 0) || !isfinite(a[t])) return OR_ERR_ARG;
+  geom_q G;
+  local_q Lq;
+  if (!local_system(P, a[t], c, f4, sig, kind, g4, &G, &Lq)) return OR_ERR_DEGENERATE;
+  qf A[4][4], R[4][8];
+  memcpy(A, Lq.A, sizeof A);
+  for (int j = 0; j < 4; ++j) {
+    qf s = Lq.B[j];
+    for (int k = 0; k < 4; ++k) s += Lq.C[k][j] * lam[k];
+    R[j][0] = s;
+  }
+  if (!qsolve(4, A, 1, R)) return OR_ERR_DEGENERATE;
+  for (int j = 0; j < 4; ++j) U[4 * t + j] = (double)R[j][0];
+  return OR_OK;
+}
+
 /* Element recovery U(T) = A^-1 (B + C' Lambda_T), Lambda_T(k) = lambda[l(F_k)]
  * and 0 on Neumann faces (Algorithm 1, second loop). U is nE x 4. */
 int or_recover(int64_t nE, const double* coord, const int32_t* tet, const int32_t* tet_face,
@@ -501,34 +607,30 @@ int or_recover(int64_t nE, const double* coord, const int32_t* tet, const int32_
                const double* f_face, const double* gN_face, const double* lambda, double* U) {
   if (!(c > 0) || !isfinite(c)) return OR_ERR_ARG;
   for (int64_t t = 0; t < nE; ++t) {
-    double P[4][3], f4[4], g4[4];
-    int32_t sig[4], kind[4];
-    qf lam[4];
-    gather_tet(coord, tet, t, P);
-    for (int k = 0; k < 4; ++k) {
-      int32_t tf = tet_face[4 * t + k];
-      int32_t F = tf & 0x7fffffff;
-      sig[k] = (tf < 0) ? -1 : 1;
-      kind[k] = face_kind[F];
-      f4[k] = f_face[F];
-      g4[k] = gN_face ? gN_face[F] : 0.0;
-      lam[k] = face_mult[F] >= 0 ? (qf)lambda[face_mult[F]] : 0;
-    }
-    if (!(a[t] > 0) || !isfinite(a[t])) return OR_ERR_ARG;
-    geom_q G;
-    local_q Lq;
-    if (!local_system(P, a[t], c, f4, sig, kind, g4, &G, &Lq)) return OR_ERR_DEGENERATE;
-    qf A[4][4], R[4][8];
-    memcpy(A, Lq.A, sizeof A);
-    for (int j = 0; j < 4; ++j) {
-      qf s = Lq.B[j];
-      for (int k = 0; k < 4; ++k) s += Lq.C[k][j] * lam[k];
-      R[j][0] = s;
-    }
-    if (!qsolve(4, A, 1, R)) return OR_ERR_DEGENERATE;
-    for (int j = 0; j < 4; ++j) U[4 * t + j] = (double)R[j][0];
+    int st = recover_element(t, coord, tet, tet_face, face_kind, face_mult, a, c, f_face, gN_face, lambda, U);
+    if (st != OR_OK) return st;
   }
   return OR_OK;
+}
+
+/* or_recover with the elements shared out across `nthreads` threads (OpenMP);
+ * every element writes its own row of U, so U is bit-identical to
+ * or_recover's.  The first error in element order is returned. */
+int or_recover_mt(int64_t nE, const double* coord, const int32_t* tet, const int32_t* tet_face,
+                  const int8_t* face_kind, const int32_t* face_mult, const double* a, double c,
+                  const double* f_face, const double* gN_face, const double* lambda, double* U, int nthreads) {
+  if (!(c > 0) || !isfinite(c)) return OR_ERR_ARG;
+  int status = OR_OK;
+  int64_t first_bad = nE;
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
+  for (int64_t t = 0; t < nE; ++t) {
+    int st = recover_element(t, coord, tet, tet_face, face_kind, face_mult, a, c, f_face, gN_face, lambda, U);
+    if (st != OR_OK) {
+#pragma omp critical
+      if (t < first_bad) { first_bad = t; status = st; }
+    }
+  }
+  return status;
 }
 
 /* Per-element local data for the monolithic check (Eq. VectorForm): A (4x4),
@@ -577,5 +679,19 @@ int or_tet_recover(const double* P12, double a, double c, const double* f4, cons
   }
   if (!qsolve(4, A, 1, R)) return OR_ERR_DEGENERATE;
   for (int j = 0; j < 4; ++j) U4[j] = (double)R[j][0];
+  return OR_OK;
+}
+
+/* r = b - H x for a CSR matrix H (rowptr [n+1], colind, values), with each
+ * row's sum formed in binary128 and rounded once: the residual of iterative
+ * refinement, accurate beyond what an fp64 sum gives when H is ill
+ * conditioned (Eq. schur's system solved to fp64 accuracy). */
+int or_residual(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* values, const double* x,
+                const double* b, double* r) {
+  for (int64_t i = 0; i < n; ++i) {
+    qf s = (qf)b[i];
+    for (int32_t j = rowptr[i]; j < rowptr[i + 1]; ++j) s -= (qf)values[j] * (qf)x[colind[j]];
+    r[i] = (double)s;
+  }
   return OR_OK;
 }

@@ -25,8 +25,8 @@ MUTANTS = {
                      "for (int k = 0; k < 4; ++k) R[j][k] = L.C[j][k]; /* C' */"),
     "load weight": ("s += (qf)f4[k] / 3;", "s += (qf)f4[k] / 4;"),
     "rhs sign": ("g_out[k] = (double)(-s);", "g_out[k] = (double)(s);"),
-    "sigma dropped in assembly": ("sig[k] = (tf < 0) ? -1 : 1;\n      kind[k] = face_kind[F];\n      mult[k] = face_mult[F];",
-                                  "sig[k] = 1;\n      kind[k] = face_kind[F];\n      mult[k] = face_mult[F];"),
+    "sigma dropped in assembly": ("sig[k] = (tf < 0) ? -1 : 1;\n    kind[k] = face_kind[F];\n    mult[k] = face_mult[F];",
+                                  "sig[k] = 1;\n    kind[k] = face_kind[F];\n    mult[k] = face_mult[F];"),
     "b_D sign": ("rhs[face_mult[F]] += bD;", "rhs[face_mult[F]] -= bD;"),
     "recovery sign": ("for (int k = 0; k < 4; ++k) s += Lq.C[k][j] * lam[k];",
                       "for (int k = 0; k < 4; ++k) s -= Lq.C[k][j] * lam[k];"),
