@@ -1,9 +1,13 @@
 #!/usr/bin/env python3
 """Throughput of the primal hybrid FEM path on one GB300 (or N replicas).
 
-One step = the whole data-parallel path on the lognormal workload (Kuhn 3^3
-cube refined 4 levels = 3,359,232 tets, a_K = exp(N(0,1)) seed 2, c = 0.1,
-f from u = sin(pi x) sin(pi y) sin(pi z), zero Dirichlet):
+One step = the whole data-parallel path on one synthetic workload.  The
+default is the jittered checkerboard (Kuhn 1^3 cube refined 6 levels =
+17,915,904 tets, interior vertices moved by up to 0.2 h with seed 3,
+a_K in {1, 1e4} on an 8^3 checkerboard, c = 1); the lognormal one (Kuhn 3^3
+cube refined 4 levels = 3,359,232 tets, a_K = exp(N(0,1)) seed 2, c = 0.1) is
+``--workload lognormal_3m``.  Both use f from u = sin(pi x) sin(pi y)
+sin(pi z) and zero Dirichlet data.  The step:
 
     ph_mesh_create  face-to-tet connectivity, numbering, CSR pattern, geometry
     ph_assemble     local matrices + element condensation + CSR scatter
@@ -17,7 +21,7 @@ buffers with the copies inside the timed region.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
-bounded sample of the same workload.
+bounded sample of the same workload, on every host core.
 """
 from __future__ import annotations
 
@@ -41,16 +45,20 @@ import meshgen  # noqa: E402
 
 METRIC = "tets assembled+condensed/s"
 UNIT = "tets/s"
-WORKLOAD = "lognormal_3m"
-# smaller case of the same recipe (Kuhn 2^3 refined 4 levels, 995,328 tets;
-# working set above L2) for profiler captures
-WORKLOADS = {"lognormal_3m": (3, 4), "lognormal_1m": (2, 4)}
+WORKLOAD = "jitter_checker_18m"
+# (Kuhn m, refinement levels) of each workload; lognormal_1m is a smaller case
+# of the lognormal recipe (995,328 tets, working set above L2) for profiler
+# captures
+WORKLOADS = {"jitter_checker_18m": (1, 6), "lognormal_3m": (3, 4), "lognormal_1m": (2, 4)}
 L2_BYTES = 129 * 2 ** 20
 HBM_PEAK_FALLBACK = 6800.0
 # FP64 peak derived from the recipe's nominal 1.25 TFLOP/s, 152 SMs and the
 # 2070 MHz maximum SM clock: 2 FP64 instructions (DFMA, DADD or DMUL) per SM
-# per clock -> 152 * 2 * 2.07e9 = 629.3e9 FP64 operations/s.
-FP64_PEAK_GOPS = 152 * 2 * 2.070
+# per clock -> 152 * 2 * 2.07e9 = 629.3e9 FP64 operations/s.  Context only:
+# the roofline takes the peak measured by ph_fp64_peak in the same run.
+FP64_PEAK_DERIVED_GOPS = 152 * 2 * 2.070
+# DFMA iterations per thread of one ph_fp64_peak launch (tens of ms)
+FP64_PEAK_ITERS = 4000
 # FP64 operations per element in k_assemble's formulas (each fma, add, mul or
 # div counted once): condensation kernel Qf 56, load and right-hand side 30,
 # condensed entries 24 (d_k (Q_km d_m + e_m) for the 10 entries, e_m = d_m/(c|T|)).
@@ -89,11 +97,12 @@ def assemble_sources_sha256():
     return h.hexdigest()
 
 
-def profile_traffic(nE):
-    """DRAM bytes of one k_assemble launch over nE elements: the per-element
-    figure of the committed ncu capture (taken on a smaller mesh of the same
-    recipe; traffic grows in proportion to the elements) times nE.  None when
-    the kernel's sources changed after the counters were taken."""
+def profile_figures():
+    """Per-element figures of the committed ncu capture of k_assemble (taken
+    on a smaller mesh of the lognormal recipe; the kernel's work and traffic
+    per element do not depend on the mesh size): DRAM bytes and FP64
+    instructions per element.  Empty when the kernel's sources changed after
+    the counters were taken."""
     prof = os.path.join(ROOT, "profiles", "k_assemble_lognormal_1m.txt")
     try:
         kv = {}
@@ -101,11 +110,17 @@ def profile_traffic(nE):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-        if kv.get("sources_sha256") != assemble_sources_sha256():
-            return None
-        return float(kv["dram_bytes_per_tet"]) * nE
-    except (OSError, KeyError, ValueError):
-        return None
+    except OSError:
+        return {}
+    if kv.get("sources_sha256") != assemble_sources_sha256():
+        return {}
+    out = {}
+    for key in ("dram_bytes_per_tet", "fp64_inst_per_tet"):
+        try:
+            out[key] = float(kv[key])
+        except (KeyError, ValueError):
+            pass
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -178,9 +193,17 @@ def whole_job_rate(units_per_rank, world, ms):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def host_cores():
+    """Host cores this process may run on (the box's, or its allotment)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def make_problem(name):
-    if name == WORKLOAD:
-        return meshgen.problem(WORKLOAD)
+    if name in ("jitter_checker_18m", "lognormal_3m"):
+        return meshgen.problem(name)
     m, k = WORKLOADS[name]
     coord, tet = meshgen.kuhn_cube(m)
     coord, tet, _ = meshgen.refined(coord, tet, k)
@@ -281,6 +304,11 @@ def gpu_arm(args, rank, world, local_rank):
     for name in BUILD_KERNELS:
         ms, n = ph.ph_kernel_time(name, reset=True)
         build_kern[name] = ms / 5 if n else float("nan")  # per build (k_scan: all scans of one build)
+    # the FP64 pipe's throughput on this GPU, measured now, under the same
+    # clock sampling as the timed steps: best of 3 probe launches
+    ph.ph_fp64_peak(FP64_PEAK_ITERS)
+    peak_runs = [ph.ph_fp64_peak(FP64_PEAK_ITERS) for _ in range(3)]
+    fp64_peak_gops = max(r[0] for r in peak_runs) / 1e9
     barrier()
     clk = clocks.stop()
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
@@ -345,15 +373,21 @@ def gpu_arm(args, rank, world, local_rank):
     # max over ranks
     ms_per_step, e2e_ms, e2e_serial_ms, asm_max, k_asm = max_over_ranks(
         [ms_per_step, e2e_ms, e2e_serial_ms, float(np.mean(asm_ms)), kern["k_assemble"]], world, dev)
+    # the lowest FP64 peak over the ranks
+    fp64_peak_gops = -max_over_ranks([-fp64_peak_gops], world, dev)[0]
 
     if rank != 0:
         return None
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
     asm_s = k_asm * 1e-3          # one k_assemble launch, CUDA events on its stream
-    ops = ASSEMBLE_OPS_PER_TET * nE
-    achieved_gops = ops / asm_s / 1e9
-    traffic = profile_traffic(nE)
+    prof = profile_figures()
+    if "fp64_inst_per_tet" in prof:
+        ops_per_tet, ops_source = prof["fp64_inst_per_tet"], "ncu FP64 instructions (DFMA+DADD+DMUL) per element"
+    else:
+        ops_per_tet, ops_source = ASSEMBLE_OPS_PER_TET, "formula count (no capture of the current sources)"
+    achieved_gops = ops_per_tet * nE / asm_s / 1e9
+    traffic = prof["dram_bytes_per_tet"] * nE if "dram_bytes_per_tet" in prof else None
     bpt = assemble_bytes_per_tet(nE, p.nC, nF)
     value = whole_job_rate(nE, world, ms_per_step)
     cfg = workload_config(args.workload, p, world)
@@ -381,12 +415,16 @@ def gpu_arm(args, rank, world, local_rank):
             "kernel": "k_assemble (average launch over the timed steps, CUDA events on its stream)",
             "bound": "alu",
             "achieved": achieved_gops,
-            "peak": FP64_PEAK_GOPS,
+            "peak": fp64_peak_gops,
             "unit": "G FP64-op/s",
-            "frac": achieved_gops / FP64_PEAK_GOPS,
+            "frac": achieved_gops / fp64_peak_gops,
             "traffic": traffic,
-            "ops_per_tet": ASSEMBLE_OPS_PER_TET,
-            "peak_source": "derived: 152 SMs x 2 FP64 inst/clk x 2070 MHz (nominal FP64 1.25 TFLOP/s)",
+            "ops_per_tet": ops_per_tet,
+            "ops_source": ops_source,
+            "peak_source": "measured in this run: ph_fp64_peak (16 independent DFMA chains per thread, 8 x 256 "
+                           "threads per SM, CUDA events), best of 3, during the clock sampling",
+            "peak_runs_gops": [r[0] / 1e9 for r in peak_runs],
+            "peak_derived_gops": FP64_PEAK_DERIVED_GOPS,
         },
         "roofline_hbm": {
             "achieved": bpt * nE / asm_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -408,7 +446,7 @@ def gpu_arm(args, rank, world, local_rank):
         line["batched"] = batched_section(ph, dev, steps=max(3, args.steps // 10), warmup=3)
         line["adjoint"] = adjoint_section(ph, dev)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(p, args.workload, budget_s=args.cpu_budget)
     return line
 
 
@@ -555,7 +593,10 @@ def oracle_sample(p, n_tets):
     return coord_s, tet_s, p.a[:n_tets]
 
 
-def oracle_step(p, coord_s, tet_s, a_s):
+def oracle_step(p, coord_s, tet_s, a_s, nthreads):
+    """One pass of the oracle over a sub-mesh: faces, multipliers, CSR
+    pattern, face data, assembly and condensation, recovery (element loops
+    on nthreads host threads)."""
     import oracle
     fc = oracle.faces(tet_s, coord_s.shape[0])
     fm, L = oracle.multipliers(fc["face_kind"])
@@ -563,32 +604,46 @@ def oracle_step(p, coord_s, tet_s, a_s):
     cen = oracle.face_centroids(coord_s, fc["face_vtx"])
     f = np.asarray(p.f(cen), np.float64)
     csr = {"face_mult": fm, "L": L, "rowptr": rowptr, "colind": colind}
-    oracle.assemble(coord_s, tet_s, fc, csr, a_s, p.c, f)
+    oracle.assemble(coord_s, tet_s, fc, csr, a_s, p.c, f, nthreads=nthreads)
     lam = np.random.default_rng(7).standard_normal(L)
-    oracle.recover(coord_s, tet_s, fc, fm, a_s, p.c, f, lam)
+    oracle.recover(coord_s, tet_s, fc, fm, a_s, p.c, f, lam, nthreads=nthreads)
 
 
-def cpu_baseline(p, budget_s=15.0, steps=1):
-    """Time the oracle as it stands (single thread) on a sample sized to
-    about budget_s seconds of CPU work."""
-    import oracle
-    oracle.build()
-    n = 2000
+def sized_oracle_run(p, budget_s, nthreads, steps=1):
+    """Size a prefix sub-mesh to about budget_s seconds per pass at nthreads,
+    then time `steps` passes.  Returns (tets, mean seconds per pass)."""
+    n = 20000
     coord_s, tet_s, a_s = oracle_sample(p, n)
     t0 = time.perf_counter()
-    oracle_step(p, coord_s, tet_s, a_s)
+    oracle_step(p, coord_s, tet_s, a_s, nthreads)
     dt = time.perf_counter() - t0
-    n = int(min(p.nE, max(2000, n * budget_s / max(dt, 1e-6) / max(steps, 1))))
+    n = int(min(p.nE, max(20000, n * budget_s / max(dt, 1e-6))))
     coord_s, tet_s, a_s = oracle_sample(p, n)
     times = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        oracle_step(p, coord_s, tet_s, a_s)
+        oracle_step(p, coord_s, tet_s, a_s, nthreads)
         times.append(time.perf_counter() - t0)
-    t = float(np.mean(times))
-    return {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {n} tets of the {WORKLOAD} mesh as a sub-mesh: faces, multipliers, CSR pattern, "
-                      f"assembly+condensation (binary128 per element), recovery; {t:.2f} s per pass"}
+    return n, float(np.mean(times))
+
+
+def cpu_baseline(p, workload, budget_s=15.0):
+    """Time the oracle as it stands on every host core (its element loops
+    shared out by OpenMP; faces and CSR pattern are serial sorts), and on
+    one core for the speed-up, each on a prefix sample sized to about
+    budget_s/2 seconds of work."""
+    import oracle
+    oracle.build()
+    cores = host_cores()
+    n_all, t_all = sized_oracle_run(p, budget_s / 2, cores)
+    n_one, t_one = sized_oracle_run(p, budget_s / 2, 1)
+    what = ("faces, multipliers, CSR pattern, assembly+condensation (binary128 per element), recovery")
+    return {"value": n_all / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n_all} tets of the {workload} mesh as a sub-mesh: {what}; {t_all:.2f} s per pass "
+                      f"on {cores} threads",
+            "single_thread": {"value": n_one / t_one, "cores": 1,
+                              "sample": f"first {n_one} tets, {t_one:.2f} s per pass"},
+            "speedup": (n_all / t_all) / (n_one / t_one)}
 
 
 def profile_pcg(iters):
@@ -616,6 +671,39 @@ def profile_pcg(iters):
     return 0
 
 
+def profile_kernels(workload, reps):
+    """Profiler target for the element kernels besides k_assemble: on the
+    given workload, `reps` rounds of assembly with the element factor,
+    recovery from a seeded Lambda, the misfit, the adjoint right-hand side and
+    the adjoint gradient from a seeded q (no solves, so few launches)."""
+    import torch
+    import paper_2509_11133_gb300 as ph
+    from paper_2509_11133_gb300 import build
+    build.build()
+    ph.load()
+    dev = torch.device("cuda", 0)
+    p = make_problem(workload)
+    mesh = ph.Mesh(torch.as_tensor(p.coord, device=dev), torch.as_tensor(p.tet, device=dev))
+    cen = mesh.faces()["face_centroid"].cpu().numpy()
+    f = torch.as_tensor(np.asarray(p.f(cen), np.float64), device=dev)
+    a = torch.as_tensor(p.a, device=dev)
+    rng = np.random.default_rng(7)
+    lam = torch.as_tensor(rng.standard_normal(mesh.L), device=dev)
+    q = torch.as_tensor(rng.standard_normal(mesh.L), device=dev)
+    u_obs = torch.as_tensor(rng.standard_normal((mesh.nE, 4)), device=dev)
+    for _ in range(reps):
+        values, rhs, factor = mesh.assemble(a, p.c, f, factor=True)
+        u = mesh.recover_factored(factor, p.c, f, lam)
+        mesh.misfit(u, u_obs)
+        mesh.adjoint_rhs(factor, p.c, u, u_obs)
+        mesh.adjoint_grad(a, factor, p.c, u, u_obs, q)
+    torch.cuda.synchronize()
+    mesh.check()
+    print(json.dumps({"profile_kernels": {"workload": workload, "nE": mesh.nE, "reps": reps}}))
+    mesh.close()
+    return 0
+
+
 def workload_config(workload, p, world):
     """The config object of both arms.  Counts of the all-Dirichlet Kuhn
     mesh in closed form: 12 m^2 4^k boundary faces, nF = (4 nE + boundary)/2,
@@ -624,11 +712,19 @@ def workload_config(workload, p, world):
     m, k = p.info["m"], p.info["k"]
     nE = p.nE
     nF = (4 * nE + 12 * m * m * 4 ** k) // 2
+    if workload == "jitter_checker_18m":
+        mesh = (f"Kuhn {m}^3 unit cube, {k} levels of the paper's 1->12 refinement, interior vertices moved "
+                f"uniformly in a ball of 0.2 x their shortest edge (seed 3; {p.info.get('jitter_redrawn', 0)} "
+                f"vertices redrawn with a halved radius)")
+        coef = "a in {1, 1e4} on an 8^3 checkerboard of element centroids"
+    else:
+        mesh = f"Kuhn {m}^3 unit cube, {k} levels of the paper's 1->12 refinement"
+        coef = "exp(N(0,1)) per element, seed 2"
     return {
         "workload": workload,
-        "mesh": f"Kuhn {m}^3 unit cube, {k} levels of the paper's 1->12 refinement",
+        "mesh": mesh,
         "nE": nE, "nC": p.nC, "nF": nF, "L": nF, "nnz": nF + 12 * nE,
-        "a": "exp(N(0,1)) per element, seed 2", "c": p.c, "f": "(3 pi^2 + 1) sin(pi x) sin(pi y) sin(pi z)",
+        "a": coef, "c": p.c, "f": "(3 pi^2 + 1) sin(pi x) sin(pi y) sin(pi z)",
         "boundary": "zero Dirichlet",
         "step": "mesh build (faces, multipliers, CSR pattern, geometry) + assembly and condensation "
                 "(with element factor) + element recovery from a seeded Lambda",
@@ -641,32 +737,34 @@ def reference_arm(args):
     p = make_problem(args.workload)
     import oracle
     oracle.build()
-    # size one step to ~budget seconds, then W + K steps
-    budget = max(1.0, args.ref_step_s)
-    n = 2000
+    cores = host_cores()
+    # size one step to ~budget seconds on every core, then W + K steps
+    budget = max(0.1, args.ref_step_s)
+    n = 20000
     coord_s, tet_s, a_s = oracle_sample(p, n)
     t0 = time.perf_counter()
-    oracle_step(p, coord_s, tet_s, a_s)
+    oracle_step(p, coord_s, tet_s, a_s, cores)
     dt = time.perf_counter() - t0
-    n = int(min(p.nE, max(2000, n * budget / max(dt, 1e-6))))
+    n = int(min(p.nE, max(20000, n * budget / max(dt, 1e-6))))
     coord_s, tet_s, a_s = oracle_sample(p, n)
     for _ in range(args.warmup):
-        oracle_step(p, coord_s, tet_s, a_s)
+        oracle_step(p, coord_s, tet_s, a_s, cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle_step(p, coord_s, tet_s, a_s)
+        oracle_step(p, coord_s, tet_s, a_s, cores)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
     value = n / (ms * 1e-3)
     sample = (f"first {n} tets of the {args.workload} mesh as a sub-mesh per step: faces, multipliers, CSR pattern, "
-              f"assembly+condensation, recovery (single-threaded C oracle, binary128 per element)")
+              f"assembly+condensation, recovery (C oracle, binary128 per element, element loops on {cores} "
+              f"threads)")
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args.workload, p, 1),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -685,6 +783,9 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=3.0)
     ap.add_argument("--profile-pcg", type=int, default=0, metavar="N",
                     help="profiler target: N Schwarz-PCG iterations on the adjoint workload, then exit")
+    ap.add_argument("--profile-kernels", type=int, default=0, metavar="R",
+                    help="profiler target: R rounds of the element kernels (assembly, recovery, misfit, adjoint) "
+                         "on --workload, then exit")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -693,6 +794,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.profile_pcg > 0:
         return profile_pcg(args.profile_pcg)
+    if args.profile_kernels > 0:
+        return profile_kernels(args.workload, args.profile_kernels)
     if args.impl == "reference":
         if rank != 0:
             return 0

@@ -65,7 +65,7 @@ typedef enum {
   PH_ERR_NOMEM = 5,          /* device allocation failed                      */
   PH_ERR_CUDA = 6,           /* a CUDA runtime call failed                    */
   PH_ERR_NOT_CONVERGED = 7,  /* the iterative solve hit its iteration cap     */
-  PH_ERR_TIMEOUT = 8         /* reserved for bounded device-side waits         */
+  PH_ERR_TIMEOUT = 8         /* a bounded device-side wait ran out            */
 } ph_status;
 
 /* Counts of a mesh.  nnz is the number of stored entries of H. */
@@ -102,6 +102,28 @@ typedef struct {
  */
 ph_status ph_mesh_create(const double* coord, int64_t nC, const int32_t* tet, int64_t nE,
                          const int32_t* neumann, int64_t nN, void* stream, ph_mesh** out);
+
+/*
+ * Build n meshes at once (not in the paper: the batched path).  The same
+ * result as n ph_mesh_create calls -- each out[p] is bit-identical in every
+ * array to ph_mesh_create on problem p -- from one enqueued build of the
+ * problems' disjoint union and one host synchronisation, instead of n.
+ *   coord[p], tet[p], neumann[p] (neumann NULL, or neumann[p] NULL with
+ *   nN[p] = 0; nN itself may be NULL): DEVICE pointers of problem p, as in
+ *   ph_mesh_create; nC[p], nE[p], nN[p]: host arrays of its sizes.
+ *   out[p] (host array of n handles) out: the meshes, usable with every entry
+ *   point.  They share one device allocation, released when the last of them
+ *   is passed to ph_mesh_destroy (in any order), and one status word:
+ *   ph_mesh_check on any of them reports (and clears) an error recorded by a
+ *   kernel on any of them.
+ * Synchronises `stream` once at the end of the union's build.  Errors as
+ * ph_mesh_create for any problem (then no mesh is returned); PH_ERR_OVERFLOW
+ * when the union exceeds ph_mesh_create's limits (16 sum nE + sum nN or sum nC
+ * reaching 2^31 - 1).
+ */
+ph_status ph_mesh_create_batch(int32_t n, const double* const* coord, const int64_t* nC, const int32_t* const* tet,
+                               const int64_t* nE, const int32_t* const* neumann, const int64_t* nN, void* stream,
+                               ph_mesh** out);
 
 /* Free a mesh.  Its device memory is released in `stream` order. */
 ph_status ph_mesh_destroy(ph_mesh* mesh, void* stream);
@@ -215,12 +237,17 @@ ph_status ph_solve_pcg(int64_t n, const int32_t* rowptr, const int32_t* colind, 
  *   ph_last_error_message() then names the limit.
  * - The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any stream
- *   capture.
+ *   capture.  The address is kept for the life of the process: like the
+ *   library's memory pools, it belongs to the device's primary context, so
+ *   the library must not be used across a cudaDeviceReset.  Devices 0..63
+ *   only (PH_ERR_ARG, with a message, beyond).
  * - All calls share the one array, which keeps the previous call's contents
  *   (each call re-initialises what it reads).  Calls that overlap on the GPU,
  *   from several streams or threads, race on it: serialise them.
- * Never calls cudaMalloc, cudaFree or any allocating routine.  Synchronises
- * `stream` every 8 iterations, like ph_solve_pcg.
+ * Never calls cudaMalloc, cudaFree or any allocating routine.  Like
+ * ph_solve_pcg, it copies the convergence test's scalars to the host and
+ * waits for `stream` every 8 iterations, so it returns only when the solve is
+ * done.
  */
 ph_status ph_solve_pcg_noalloc(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* values,
                                const double* b, double* x, double rtol, int32_t maxit, int32_t* iters,
@@ -308,6 +335,32 @@ ph_status ph_schwarz_create(const ph_mesh* mesh, const double* values, void* str
 ph_status ph_schwarz_destroy(ph_schwarz* P, void* stream);
 ph_status ph_solve_pcg_schwarz(const ph_mesh* mesh, const double* values, const ph_schwarz* P, const double* b,
                                double* x, double rtol, int32_t maxit, int32_t* iters, double* relres, void* stream);
+
+/*
+ * Solve H Lambda = rhs to fp64 accuracy by iterative refinement (an
+ * addition: the paper solves with a direct method).  A plain fp64 solve of the
+ * condensed system stops at an error of about cond(H) eps, which exceeds 1e-9
+ * on ill-conditioned meshes (the jittered a in {1, 1e4} checkerboard).  Here:
+ *     x = 0, r = rhs;  repeat:  solve H d = r by PCG to inner_rtol;  x += d;
+ *     stop when ||d|| <= tol ||x||;  r = rhs - H x,
+ * with the residual's row sums accumulated in double-word arithmetic (exact
+ * products by fma, compensated sums), so x converges to the fp64 rounding of
+ * the exact solution of the system as given.
+ *   mesh, values: the condensed system (ph_assemble output, n = L).
+ *   P: Schwarz preconditioner of the same mesh and values, or NULL for Jacobi.
+ *   tol: relative size of the last correction (e.g. 1e-15); inner_rtol: the
+ *   PCG tolerance of each correction solve (e.g. 1e-8); max_steps >= 1
+ *   refinement steps; maxit: PCG iteration cap of each correction solve.
+ *   steps, iters, correction (host, may be NULL): refinement steps taken, PCG
+ *   iterations in total, the last relative correction.
+ * Allocates its workspace from the library's pool; synchronises `stream`
+ * inside each PCG solve and once per step.  PH_ERR_NOT_CONVERGED when the
+ * last correction is still above tol after max_steps (x holds the last
+ * iterate).
+ */
+ph_status ph_solve_refined(const ph_mesh* mesh, const double* values, const ph_schwarz* P, const double* b,
+                           double* x, double tol, double inner_rtol, int32_t max_steps, int32_t maxit,
+                           int32_t* steps, int32_t* iters, double* correction, void* stream);
 
 /*
  * y = H x for a CSR matrix (rowptr [n+1], colind, values) and x [n], y [n]
@@ -399,6 +452,44 @@ ph_status ph_assemble_host(const double* coord, int64_t nC, const int32_t* tet, 
  */
 ph_status ph_timing_enable(int on);
 ph_status ph_kernel_time(const char* kernel, int reset, double* ms, int64_t* launches);
+
+/*
+ * Test hooks (not in the paper): they let tests exercise the error paths of
+ * the library without faulting or hanging a GPU.
+ *   ph_test_fail_alloc(after): the (after+1)-th device allocation from the
+ *     library's pool from now on fails as if the device were out of memory
+ *     (the call that made it returns PH_ERR_NOMEM and frees what it had
+ *     taken); after < 0 switches the hook off.  Later allocations succeed.
+ *   ph_test_scan_withhold(on): while on, the device-wide scans of
+ *     ph_mesh_create (and of the Schwarz set-up) run with their tile 1 never
+ *     publishing its partial sum and a look-back poll limit of 2^12, so the
+ *     wait of the tiles after it runs out: they record PH_ERR_TIMEOUT in the
+ *     status word and return (every wait in the scan is bounded; nothing
+ *     hangs).  Scans of fewer than three tiles (4096 values each) are not
+ *     affected.  Off by default; for tests only.
+ *   ph_pool_in_use(bytes): (host) bytes of the current device's library pool
+ *     held by live allocations (freed memory counts once its stream-ordered
+ *     free has run), to check that failed calls leak nothing.
+ * The hooks are process-wide and not synchronised with calls in flight on
+ * other threads.
+ */
+ph_status ph_test_fail_alloc(int64_t after);
+ph_status ph_test_scan_withhold(int on);
+ph_status ph_pool_in_use(int64_t* bytes);
+
+/*
+ * Measure the FP64 pipe's throughput on the current device (not in the paper;
+ * it gives the element kernels' roofline its denominator).  One kernel of
+ * 8 blocks of 256 threads per SM, each thread running 16 independent chains
+ * of `iters` DFMA operations, timed with a pair of CUDA events on `stream`.
+ *   iters      > 0; about 4000 gives a launch of tens of milliseconds.
+ *   ops_per_s  (host) out: DFMA operations per second over the whole GPU
+ *              (one fused multiply-add counts as one operation).
+ *   ms         (host, may be NULL) out: the launch's duration.
+ * Allocates a small result buffer from the library's pool and synchronises
+ * `stream`.
+ */
+ph_status ph_fp64_peak(int64_t iters, double* ops_per_s, double* ms, void* stream);
 
 /*
  * y[i] = 1/x[i] with the device reciprocal the element kernels use for

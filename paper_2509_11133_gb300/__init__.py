@@ -34,7 +34,8 @@ EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces",
            "ph_batch_assemble", "ph_batch_autotune", "ph_batch_set_config", "ph_batch_get_config",
            "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy", "ph_rcp", "ph_half_sqrt", "ph_timing_enable",
            "ph_kernel_time", "ph_assemble_host", "ph_schwarz_create", "ph_schwarz_destroy",
-           "ph_solve_pcg_schwarz")
+           "ph_solve_pcg_schwarz", "ph_fp64_peak", "ph_test_fail_alloc", "ph_test_scan_withhold",
+           "ph_pool_in_use", "ph_solve_refined", "ph_mesh_create_batch")
 
 
 class PHError(RuntimeError):
@@ -66,6 +67,7 @@ def load(path: str | None = None):
     P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     sig = {
         "ph_mesh_create": [P, I64, P, I64, P, I64, P, ctypes.POINTER(P)],
+        "ph_mesh_create_batch": [I32, P, P, P, P, P, P, P, P],
         "ph_mesh_destroy": [P, P],
         "ph_mesh_info": [P, ctypes.POINTER(ph_info)],
         "ph_mesh_faces": [P, P, P, P, P, P, P, P, P],
@@ -94,6 +96,12 @@ def load(path: str | None = None):
         "ph_refined_destroy": [P, P],
         "ph_rcp": [P, I64, P, P],
         "ph_half_sqrt": [P, I64, P, P],
+        "ph_fp64_peak": [I64, ctypes.POINTER(D), ctypes.POINTER(D), P],
+        "ph_test_fail_alloc": [I64],
+        "ph_test_scan_withhold": [ctypes.c_int],
+        "ph_pool_in_use": [ctypes.POINTER(I64)],
+        "ph_solve_refined": [P, P, P, P, P, D, D, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I32),
+                             ctypes.POINTER(D), P],
         "ph_timing_enable": [ctypes.c_int],
         "ph_kernel_time": [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(D), ctypes.POINTER(I64)],
         "ph_assemble_host": [P, I64, P, I64, P, I64, I64, I64, I64, P, D, P, P, P, P, P, P, P, P, P, P],
@@ -221,6 +229,23 @@ class Schwarz:
             pass
 
 
+def solve_refined(mesh, values, rhs, P=None, x=None, tol=1e-15, inner_rtol=1e-8, max_steps=20, maxit=100000,
+                  stream=None, check=True):
+    """H x = rhs to fp64 accuracy by iterative refinement (double-word
+    residual) around PCG, Schwarz-preconditioned with P (a Schwarz) or Jacobi
+    (P None).  Returns (x, steps, iterations, last relative correction, status)."""
+    n = rhs.numel()
+    if x is None:
+        x = torch.empty(n, dtype=torch.float64, device=rhs.device)
+    st, it, corr = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0)
+    code = load().ph_solve_refined(mesh.handle, _ptr(values), None if P is None else P._h, _ptr(rhs), _ptr(x),
+                                   float(tol), float(inner_rtol), int(max_steps), int(maxit), ctypes.byref(st),
+                                   ctypes.byref(it), ctypes.byref(corr), _stream(stream))
+    if check:
+        _check(code, "ph_solve_refined")
+    return x, st.value, it.value, corr.value, code
+
+
 def ph_spmv(rowptr, colind, values, x, y=None, stream=None):
     n = x.numel()
     y = torch.empty_like(x) if y is None else y
@@ -251,8 +276,19 @@ class Mesh:
         _check(L.ph_mesh_create(_ptr(coord), coord.shape[0], _ptr(tet), tet.shape[0], _ptr(nb),
                                 0 if nb is None else nb.shape[0], _stream(stream), ctypes.byref(h)),
                "ph_mesh_create")
+        self._adopt(h, coord.device)
+
+    @classmethod
+    def _from_handle(cls, h, device):
+        m = cls.__new__(cls)
+        m._h = None
+        m._adopt(h, device)
+        return m
+
+    def _adopt(self, h, device):
+        L = load()
         self._h = h
-        self.device = coord.device
+        self.device = device
         inf = ph_info()
         _check(L.ph_mesh_info(h, ctypes.byref(inf)), "ph_mesh_info")
         self.info = {f: int(getattr(inf, f)) for f, _ in ph_info._fields_}
@@ -374,6 +410,29 @@ def ph_mesh_create(coord, tet, neumann=None, stream=None) -> Mesh:
     return Mesh(coord, tet, neumann, stream)
 
 
+def create_meshes(coords, tets, neumanns=None, stream=None):
+    """Build many meshes in one batched enqueue (ph_mesh_create_batch): lists
+    of CUDA tensors (coord nC x 3 float64, tet nE x 4 int32, neumann nN x 3
+    int32 or None).  Returns a list of Mesh objects sharing one allocation."""
+    n = len(coords)
+    coords = [c.contiguous() for c in coords]
+    tets = [t.contiguous() for t in tets]
+    nbs = [None if (neumanns is None or nb is None or nb.numel() == 0) else nb.contiguous()
+           for nb in (neumanns or [None] * n)]
+    for c, t, nb in zip(coords, tets, nbs):
+        if c.dtype != torch.float64 or t.dtype != torch.int32 or (nb is not None and nb.dtype != torch.int32):
+            raise ValueError("coord float64, tet and neumann int32")
+    arr = lambda xs: _ptr_array(xs)
+    i64 = lambda xs: (ctypes.c_int64 * max(n, 1))(*xs)
+    handles = (ctypes.c_void_p * max(n, 1))()
+    _check(load().ph_mesh_create_batch(n, arr(coords), i64([c.shape[0] for c in coords]), arr(tets),
+                                       i64([t.shape[0] for t in tets]), arr(nbs),
+                                       i64([0 if nb is None else nb.shape[0] for nb in nbs]), _stream(stream),
+                                       handles), "ph_mesh_create_batch")
+    dev = coords[0].device if n else torch.device("cuda")
+    return [Mesh._from_handle(ctypes.c_void_p(handles[i]), dev) for i in range(n)]
+
+
 def _hptr(t):
     """Address of a contiguous CPU tensor (host buffer), or None."""
     if t is None:
@@ -431,6 +490,31 @@ def ph_half_sqrt(x, stream=None):
     y = torch.empty_like(x)
     _check(load().ph_half_sqrt(_ptr(x), x.numel(), _ptr(y), _stream(stream)), "ph_half_sqrt")
     return y
+
+
+def ph_test_fail_alloc(after):
+    """Test hook: the (after+1)-th next pool allocation fails (after < 0: off)."""
+    _check(load().ph_test_fail_alloc(int(after)), "ph_test_fail_alloc")
+
+
+def ph_test_scan_withhold(on):
+    """Test hook: scans withhold one tile's publication (bounded waits run out)."""
+    _check(load().ph_test_scan_withhold(1 if on else 0), "ph_test_scan_withhold")
+
+
+def ph_pool_in_use() -> int:
+    """Bytes held by live allocations of the library's pool on this device."""
+    n = ctypes.c_int64()
+    _check(load().ph_pool_in_use(ctypes.byref(n)), "ph_pool_in_use")
+    return n.value
+
+
+def ph_fp64_peak(iters=4000, stream=None):
+    """(DFMA operations per second, launch ms) of the library's FP64
+    throughput probe on the current device."""
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().ph_fp64_peak(int(iters), ctypes.byref(ops), ctypes.byref(ms), _stream(stream)), "ph_fp64_peak")
+    return ops.value, ms.value
 
 
 def ph_refine(coord, tet, lists=None, stream=None):

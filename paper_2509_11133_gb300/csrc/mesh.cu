@@ -14,6 +14,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <initializer_list>
+#include <vector>
+
 
 #include "ph_internal.cuh"
 
@@ -478,9 +481,49 @@ using namespace ph;
 
 static void mesh_free(ph_mesh* m, cudaStream_t s) {
   if (!m) return;
-  free_async(m->arena, s);
+  if (m->shared) {
+    if (m->shared->refs.fetch_sub(1) == 1) {
+      free_async(m->shared->arena, s);
+      free_async(m->shared->extra, s);
+      delete m->shared;
+    }
+  } else {
+    free_async(m->arena, s);
+  }
   delete m;
 }
+
+// Per-problem counts of a batched build (the union mesh of ph_mesh_create_batch):
+// problem p owns tets [toff[p], toff[p+1]); a face belongs to the problem of
+// its T+ tet.  counts[3p..3p+2] += faces, multipliers, CSR entries of rows.
+__global__ void k_batch_counts(const int2* __restrict__ face_tet, const int32_t* __restrict__ face_mult,
+                               const int32_t* __restrict__ rowptr, const int64_t* __restrict__ d_tot, int64_t nFmax,
+                               const int64_t* __restrict__ toff, int32_t n, unsigned long long* __restrict__ counts,
+                               const unsigned* status) {
+  const int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (F >= nFmax || F >= d_tot[0] || failed(status)) return;
+  const int64_t t = face_tet[F].x;
+  int lo = 0, hi = n - 1;  // last p with toff[p] <= t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (toff[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  atomicAdd(&counts[3 * lo], 1ull);
+  const int l = face_mult[F];
+  if (l >= 0) {
+    atomicAdd(&counts[3 * lo + 1], 1ull);
+    atomicAdd(&counts[3 * lo + 2], (unsigned long long)(rowptr[l + 1] - rowptr[l]));
+  }
+}
+
+// Hook of a batched build: the per-problem counts, computed before the
+// build's one synchronisation and read with it.
+struct BatchCounts {
+  const int64_t* d_toff;  // n + 1 tet offsets (device)
+  int32_t n;
+  unsigned long long* d_counts;  // 3n, zeroed by the caller
+  unsigned long long* h_counts;  // 3n (host)
+};
 
 // Synchronise and read n device int64 counters and the status word.
 static ph_status read_counters(const int64_t* d_tot, int n, unsigned* d_status, cudaStream_t s, int64_t* tot,
@@ -498,8 +541,16 @@ static ph_status read_counters(const int64_t* d_tot, int n, unsigned* d_status, 
   } while (0)
 #define PH_CU(expr, what) PH_TRY(cuda_status((expr), what))
 
+static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet, int64_t nE, const int32_t* neumann,
+                            int64_t nN, cudaStream_t s, ph_mesh** out, const BatchCounts* bc);
+
 extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32_t* tet, int64_t nE,
                                     const int32_t* neumann, int64_t nN, void* stream, ph_mesh** out) {
+  return mesh_build(coord, nC, tet, nE, neumann, nN, (cudaStream_t)stream, out, nullptr);
+}
+
+static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet, int64_t nE, const int32_t* neumann,
+                            int64_t nN, cudaStream_t s, ph_mesh** out, const BatchCounts* bc) {
   if (!out) return PH_ERR_ARG;
   *out = nullptr;
   if (nE < 0 || nC < 0 || nN < 0 || (nE > 0 && (!coord || !tet)) || (nN > 0 && !neumann)) return PH_ERR_ARG;
@@ -509,8 +560,7 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
   // synchronises once, at the end; int32 ids and CSR positions bound the size.
   const int64_t nFmax = 4 * nE + nN, nnzmax = nFmax + 12 * nE;
   if (nnzmax >= ((int64_t)1 << 31) - 1 || nC >= ((int64_t)1 << 31) - 1) return PH_ERR_OVERFLOW;
-  cudaStream_t s = (cudaStream_t)stream;  // everything runs in order on the caller's stream
-  ph_status st = PH_OK;
+  ph_status st = PH_OK;  // everything runs in order on the caller's stream s
   // face-key buckets: 4 per largest vertex while the bucket ids stay below 2^31
   // (finer buckets shorten the match scans but cost more in the scattered
   // fill and the bucket scan than they save)
@@ -642,6 +692,13 @@ extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32
                                        m->face_area, m->status);
     PH_CU(launched(), "k_row_fill");
   }
+  if (bc && bc->n > 0 && nFmax > 0) {  // per-problem counts of a batched build
+    k_batch_counts<<<gF, kThreads, 0, s>>>(m->face_tet, m->face_mult, m->rowptr, d_tot, nFmax, bc->d_toff, bc->n,
+                                           bc->d_counts, m->status);
+    PH_CU(launched(), "k_batch_counts");
+    PH_CU(cudaMemcpyAsync(bc->h_counts, bc->d_counts, sizeof(unsigned long long) * 3 * bc->n,
+                          cudaMemcpyDeviceToHost, s), "copy");
+  }
   // the one synchronisation: counts and the first error of any kernel
   PH_TRY(read_counters(d_tot, 3, m->status, s, tot, &bits));
   }
@@ -727,4 +784,280 @@ extern "C" ph_status ph_mesh_check(ph_mesh* m, void* stream) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e, "ph_mesh_check");
   return status_from_bits(bits);
+}
+
+// ---------------------------------------------------------------------------
+// Batched build: n meshes at once.  Their disjoint union (vertex ids of
+// problem p shifted by the vertices of the problems before it) is built as one
+// mesh: faces of different problems never match, and the first-occurrence
+// numbering of the union, restricted to problem p, is p's own numbering
+// shifted by the faces of the problems before it (p's tets are consecutive);
+// the same holds for multipliers, CSR rows and CSR entries.  So one build
+// gives every problem's connectivity; a rebase pass then subtracts each
+// problem's offsets, and the per-problem meshes are views into the union's
+// memory with local ids, bit-identical to building each alone.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Offsets of problem p in the union (device, n + 1 entries each).
+struct UnionOffsets {
+  const int64_t *toff, *voff, *foff, *moff, *zoff;
+  int32_t n;
+};
+
+// last p with off[p] <= i (off ascending, off[0] = 0)
+__device__ __forceinline__ int problem_of(const int64_t* __restrict__ off, int32_t n, int64_t i) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct UnionSources {
+  const int32_t* tet;  // problem's tets (nE_p x 4)
+  const int32_t* nb;   // problem's Neumann triples or null
+};
+
+// union tets and Neumann triples: problem p's ids shifted by voff[p]
+__global__ void k_union_inputs(const UnionSources* __restrict__ src, const int64_t* __restrict__ toff,
+                               const int64_t* __restrict__ noff, const int64_t* __restrict__ voff, int32_t n,
+                               int64_t nE, int64_t nN, int4* __restrict__ tet_u, int32_t* __restrict__ nb_u) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < nE) {
+    const int p = problem_of(toff, n, i);
+    const int v = (int)voff[p];
+    const int4 t = reinterpret_cast<const int4*>(src[p].tet)[i - toff[p]];
+    tet_u[i] = make_int4(t.x + v, t.y + v, t.z + v, t.w + v);
+  } else if (i < nE + nN) {
+    const int64_t j = i - nE;
+    const int p = problem_of(noff, n, j);
+    const int v = (int)voff[p];
+    const int64_t k = j - noff[p];
+    nb_u[3 * j] = src[p].nb[3 * k] + v;
+    nb_u[3 * j + 1] = src[p].nb[3 * k + 1] + v;
+    nb_u[3 * j + 2] = src[p].nb[3 * k + 2] + v;
+  }
+}
+
+__device__ __forceinline__ int shift_id(int x, int64_t off) {  // keep bit 31 (sigma / Dirichlet mark)
+  return (int)(((unsigned)x & 0x80000000u) | (unsigned)((x & PH_ID_MASK) - (int)off));
+}
+
+// per tet: local vertex ids, face ids, multiplier ids, CSR positions
+__global__ void k_rebase_tets(UnionOffsets o, int64_t nE, int4* __restrict__ tet, int4* __restrict__ tface,
+                              int4* __restrict__ tmult, int4* __restrict__ tpos) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nE) return;
+  const int p = problem_of(o.toff, o.n, t);
+  const int v = (int)o.voff[p], z = (int)o.zoff[p];
+  const int64_t f = o.foff[p], mo = o.moff[p];
+  const int4 a = tet[t];
+  tet[t] = make_int4(a.x - v, a.y - v, a.z - v, a.w - v);
+  const int4 b = tface[t];
+  tface[t] = make_int4(shift_id(b.x, f), shift_id(b.y, f), shift_id(b.z, f), shift_id(b.w, f));
+  const int4 c = tmult[t];
+  int cm[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (cm[k] != PH_NO_MULT) cm[k] = shift_id(cm[k], mo);
+  tmult[t] = make_int4(cm[0], cm[1], cm[2], cm[3]);
+  const int4 d = tpos[t];  // positions of Neumann slots are never read
+  tpos[t] = make_int4(d.x - z, d.y - z, d.z - z, d.w - z);
+}
+
+// per face: local T+/T-, vertex ids and multiplier id
+__global__ void k_rebase_faces(UnionOffsets o, int64_t nF, int2* __restrict__ face_tet,
+                               int32_t* __restrict__ face_vtx, int32_t* __restrict__ face_mult) {
+  const int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (F >= nF) return;
+  const int p = problem_of(o.foff, o.n, F);
+  const int t0 = (int)o.toff[p], v = (int)o.voff[p];
+  const int2 ft = face_tet[F];
+  face_tet[F] = make_int2(ft.x - t0, ft.y < 0 ? -1 : ft.y - t0);
+  face_vtx[3 * F] -= v;
+  face_vtx[3 * F + 1] -= v;
+  face_vtx[3 * F + 2] -= v;
+  const int l = face_mult[F];
+  if (l >= 0) face_mult[F] = l - (int)o.moff[p];
+}
+
+// per multiplier row: the problem's own row pointers (problem p's L_p + 1
+// entries at rowptr_b + moff[p] + p) and diagonal positions
+__global__ void k_rebase_rows(UnionOffsets o, int64_t L, const int32_t* __restrict__ rowptr,
+                              int32_t* __restrict__ rowptr_b, int32_t* __restrict__ rowdiag) {
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= L + o.n) return;
+  if (l < L) {
+    const int p = problem_of(o.moff, o.n, l);
+    const int z = (int)o.zoff[p];
+    rowptr_b[l + p] = rowptr[l] - z;
+    rowdiag[l] -= z;
+  } else {  // the closing entry of problem p: its nnz
+    const int p = (int)(l - L);
+    rowptr_b[o.moff[p + 1] + p] = (int)(o.zoff[p + 1] - o.zoff[p]);
+  }
+}
+
+// per CSR entry: local column ids
+__global__ void k_rebase_cols(UnionOffsets o, int64_t nnz, int32_t* __restrict__ colind) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= nnz) return;
+  colind[j] -= (int)o.moff[problem_of(o.zoff, o.n, j)];
+}
+
+}  // namespace
+
+extern "C" ph_status ph_mesh_create_batch(int32_t n, const double* const* coord, const int64_t* nC,
+                                          const int32_t* const* tet, const int64_t* nE,
+                                          const int32_t* const* neumann, const int64_t* nN, void* stream,
+                                          ph_mesh** out) {
+  if (n < 0 || !out || (n > 0 && (!coord || !nC || !tet || !nE))) return PH_ERR_ARG;
+  for (int32_t p = 0; p < n; ++p) out[p] = nullptr;
+  if (n == 0) return PH_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  // host offsets: tets, Neumann triples, vertices
+  std::vector<int64_t> toff(n + 1, 0), noff(n + 1, 0), voff(n + 1, 0);
+  std::vector<UnionSources> src(n);
+  for (int32_t p = 0; p < n; ++p) {
+    const int64_t np = nN ? nN[p] : 0;
+    if (nE[p] < 0 || nC[p] < 0 || np < 0 || (nE[p] > 0 && (!coord[p] || !tet[p])) ||
+        (np > 0 && (!neumann || !neumann[p])) || (reinterpret_cast<uintptr_t>(tet[p]) & 15u) != 0)
+      return PH_ERR_ARG;
+    toff[p + 1] = toff[p] + nE[p];
+    noff[p + 1] = noff[p] + np;
+    voff[p + 1] = voff[p] + nC[p];
+    src[p] = UnionSources{tet[p], np > 0 ? neumann[p] : nullptr};
+  }
+  const int64_t nEu = toff[n], nNu = noff[n], nCu = voff[n];
+  if (16 * nEu + nNu >= ((int64_t)1 << 31) - 1 || nCu >= ((int64_t)1 << 31) - 1) return PH_ERR_OVERFLOW;
+  // union inputs and the offset tables in one allocation
+  Carve ic;
+  const size_t o_coord = ic.take<double>(3 * nCu), o_tet = ic.take<int4>(nEu), o_nb = ic.take<int32_t>(3 * nNu);
+  const size_t o_src = ic.take<UnionSources>(n), o_off = ic.take<int64_t>(3 * (n + 1));
+  const size_t o_cnt = ic.take<unsigned long long>(3 * n);
+  void* in = nullptr;
+  cudaError_t e = alloc_bytes(&in, ic.bytes, s);
+  if (e != cudaSuccess) return cuda_status(e, "alloc batch inputs");
+  double* coord_u = Carve::at<double>(in, o_coord);
+  int4* tet_u = Carve::at<int4>(in, o_tet);
+  int32_t* nb_u = Carve::at<int32_t>(in, o_nb);
+  UnionSources* d_src = Carve::at<UnionSources>(in, o_src);
+  int64_t* d_off = Carve::at<int64_t>(in, o_off);  // toff, noff, voff
+  unsigned long long* d_cnt = Carve::at<unsigned long long>(in, o_cnt);
+  std::vector<int64_t> offs;
+  offs.insert(offs.end(), toff.begin(), toff.end());
+  offs.insert(offs.end(), noff.begin(), noff.end());
+  offs.insert(offs.end(), voff.begin(), voff.end());
+  for (int32_t p = 0; p < n && e == cudaSuccess; ++p)
+    if (nC[p] > 0)
+      e = cudaMemcpyAsync(coord_u + 3 * voff[p], coord[p], sizeof(double) * 3 * nC[p], cudaMemcpyDeviceToDevice, s);
+  // pageable sources: the copies return once the data is staged
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_src, src.data(), sizeof(UnionSources) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_off, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * 3 * n, s);
+  if (e == cudaSuccess && nEu + nNu > 0) {
+    k_union_inputs<<<grid_for(nEu + nNu), kThreads, 0, s>>>(d_src, d_off, d_off + (n + 1), d_off + 2 * (n + 1), n,
+                                                          nEu, nNu, tet_u, nb_u);
+    e = launched();
+  }
+  if (e != cudaSuccess) {
+    free_async(in, s);
+    return cuda_status(e, "ph_mesh_create_batch inputs");
+  }
+  std::vector<unsigned long long> cnt(3 * (size_t)n, 0);
+  BatchCounts bc{d_off, n, d_cnt, cnt.data()};
+  ph_mesh* u = nullptr;
+  ph_status st = mesh_build(coord_u, nCu, reinterpret_cast<const int32_t*>(tet_u), nEu, nNu > 0 ? nb_u : nullptr,
+                            nNu, s, &u, &bc);
+  free_async(in, s);
+  if (st != PH_OK) return st;
+  // per-problem face, multiplier and CSR offsets from the counts
+  std::vector<int64_t> foff(n + 1, 0), moff(n + 1, 0), zoff(n + 1, 0);
+  for (int32_t p = 0; p < n; ++p) {
+    foff[p + 1] = foff[p] + (int64_t)cnt[3 * p];
+    moff[p + 1] = moff[p] + (int64_t)cnt[3 * p + 1];
+    zoff[p + 1] = zoff[p] + (int64_t)cnt[3 * p + 2];
+  }
+  if (foff[n] != u->nF || moff[n] != u->L || zoff[n] != u->nnz) {
+    mesh_free(u, s);
+    return PH_ERR_ARG;
+  }
+  // row pointers of the problems (L + n) and the offset tables (5 (n + 1))
+  Carve xc;
+  const size_t o_rp = xc.take<int32_t>(u->L + n), o_tab = xc.take<int64_t>(5 * (n + 1));
+  void* extra = nullptr;
+  e = alloc_bytes(&extra, xc.bytes, s);
+  if (e != cudaSuccess) {
+    mesh_free(u, s);
+    return cuda_status(e, "alloc batch rows");
+  }
+  int32_t* rowptr_b = Carve::at<int32_t>(extra, o_rp);
+  int64_t* tab = Carve::at<int64_t>(extra, o_tab);
+  std::vector<int64_t> t5;
+  for (const auto* v : {&toff, &voff, &foff, &moff, &zoff}) t5.insert(t5.end(), v->begin(), v->end());
+  e = cudaMemcpyAsync(tab, t5.data(), sizeof(int64_t) * t5.size(), cudaMemcpyHostToDevice, s);
+  const UnionOffsets o{tab, tab + (n + 1), tab + 2 * (n + 1), tab + 3 * (n + 1), tab + 4 * (n + 1), n};
+  if (e == cudaSuccess && nEu > 0) {
+    k_rebase_tets<<<grid_for(nEu), kThreads, 0, s>>>(o, nEu, u->tet, u->tface, u->tmult, u->tpos);
+    e = launched();
+  }
+  if (e == cudaSuccess && u->nF > 0) {
+    k_rebase_faces<<<grid_for(u->nF), kThreads, 0, s>>>(o, u->nF, u->face_tet, u->face_vtx, u->face_mult);
+    e = launched();
+  }
+  if (e == cudaSuccess) {
+    k_rebase_rows<<<grid_for(u->L + n), kThreads, 0, s>>>(o, u->L, u->rowptr, rowptr_b, u->rowdiag);
+    e = launched();
+  }
+  if (e == cudaSuccess && u->nnz > 0) {
+    k_rebase_cols<<<grid_for(u->nnz), kThreads, 0, s>>>(o, u->nnz, u->colind);
+    e = launched();
+  }
+  if (e != cudaSuccess) {
+    free_async(extra, s);
+    mesh_free(u, s);
+    return cuda_status(e, "ph_mesh_create_batch rebase");
+  }
+  // the views: each problem's slices of the union arrays, local ids
+  ph_mesh_shared* sh = new ph_mesh_shared();
+  sh->refs.store(n);
+  sh->arena = u->arena;
+  sh->extra = extra;
+  for (int32_t p = 0; p < n; ++p) {
+    ph_mesh* m = new ph_mesh();
+    memset(m, 0, sizeof *m);
+    const int64_t t0 = toff[p], v0 = voff[p], f0 = foff[p], m0 = moff[p], z0 = zoff[p];
+    m->device = u->device;
+    m->shared = sh;
+    m->nE = nE[p];
+    m->nC = nC[p];
+    m->nF = foff[p + 1] - f0;
+    m->L = moff[p + 1] - m0;
+    m->nnz = zoff[p + 1] - z0;
+    m->nFi = 4 * m->nE - m->nF;
+    m->nFn = m->nF - m->L;
+    m->nFd = m->nF - m->nFi - m->nFn;
+    m->coord = u->coord + 3 * v0;
+    m->tet = u->tet + t0;
+    m->tface = u->tface + t0;
+    m->tmult = u->tmult + t0;
+    m->tpos = u->tpos + t0;
+    m->trel = u->trel + t0;
+    m->geo = u->geo + PH_GEO_STRIDE * t0;
+    m->face_tet = u->face_tet + f0;
+    m->face_vtx = u->face_vtx + 3 * f0;
+    m->face_kind = u->face_kind + f0;
+    m->face_mult = u->face_mult + f0;
+    m->face_area = u->face_area + f0;
+    m->rowptr = rowptr_b + m0 + p;
+    m->colind = u->colind + z0;
+    m->rowdiag = u->rowdiag + m0;
+    m->status = u->status;
+    out[p] = m;
+  }
+  delete u;  // its arena now belongs to the views
+  return PH_OK;
 }

@@ -18,8 +18,17 @@
 // GT = G_e T0^-1 row-major (9), |det E|, 1/|det E|, padding.
 #define PH_GEO_STRIDE 18
 
+// Device memory shared by the meshes of one batched build (ph_mesh_create_batch):
+// released when the last of them is destroyed.
+struct ph_mesh_shared {
+  std::atomic<int> refs;
+  void* arena;  // the union mesh's arrays
+  void* extra;  // per-problem row pointers and offset tables
+};
+
 struct ph_mesh {
   int device;
+  ph_mesh_shared* shared;  // non-null for a mesh of a batched build (arena then unused)
   void* arena;         // one allocation holding every array below
   int64_t nE, nC, nF, nFi, nFd, nFn, L, nnz;
   double* coord;       // nC*3

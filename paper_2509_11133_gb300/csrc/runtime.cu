@@ -56,8 +56,14 @@ static cudaError_t pool_for(int dev, cudaMemPool_t* out) {
   return cudaSuccess;
 }
 
+// Test hook (ph_test_fail_alloc): the number of pool allocations still to
+// succeed before one fails; negative = never fail.
+static std::atomic<int64_t> g_fail_alloc_after{-1};
+
 cudaError_t alloc_bytes(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
+  if (g_fail_alloc_after.load(std::memory_order_relaxed) >= 0 && g_fail_alloc_after.fetch_sub(1) == 0)
+    return cudaErrorMemoryAllocation;  // the injected failure (once)
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -121,12 +127,17 @@ __device__ __forceinline__ T block_excl_scan(T v, T* total) {
 // (inputs are non-negative counts).
 constexpr unsigned long long kScanAgg = 1ull << 62, kScanInc = 2ull << 62, kScanVal = (1ull << 62) - 1;
 constexpr int kScanSpinLimit = 1 << 20;  // unready polls before giving up (>= 32 ns apart)
+// Test hook (ph_test_scan_withhold): scans run with tile 1 never publishing
+// its state and this short poll limit, so that a look-back wait runs out.
+constexpr int kScanTestSpinLimit = 1 << 12;
+static std::atomic<int> g_scan_withhold{0};
 
 __global__ void __launch_bounds__(SCAN_T) k_scan(const int32_t* in, int32_t* out, int64_t nmax,
                                                   const int64_t* __restrict__ d_len, int64_t len_add,
                                                   int64_t* __restrict__ d_total, unsigned long long* state,
                                                   unsigned* counter, unsigned* status,
-                                                  const int4* __restrict__ mates, int64_t nmates) {
+                                                  const int4* __restrict__ mates, int64_t nmates,
+                                                  int spin_limit, int64_t withhold) {
   __shared__ unsigned s_tile;
   __shared__ int64_t s_prefix;
   if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
@@ -179,19 +190,20 @@ __global__ void __launch_bounds__(SCAN_T) k_scan(const int32_t* in, int32_t* out
     volatile unsigned long long* st = state;
     const int lane = threadIdx.x;
     int64_t prefix = 0;
+    const bool publish = tile != withhold;
     if (tile > 0) {
-      if (lane == 0) st[tile] = kScanAgg | (unsigned long long)tot;
+      if (lane == 0 && publish) st[tile] = kScanAgg | (unsigned long long)tot;
       int spins = 0;
       for (int64_t p = tile - 1; p >= 0;) {
         const int64_t q = p - lane;  // lane 0 is the nearest predecessor
         unsigned long long w = kScanInc;  // before tile 0: an inclusive prefix of 0
         if (q >= 0) w = st[q];
         while (__any_sync(0xFFFFFFFFu, (w >> 62) == 0)) {
-          if (++spins > kScanSpinLimit) break;
+          if (++spins > spin_limit) break;
           __nanosleep(32);
           if ((w >> 62) == 0) w = st[q];
         }
-        if (spins > kScanSpinLimit) {  // a predecessor never published: give up, flagged
+        if (spins > spin_limit) {  // a predecessor never published: give up, flagged
           if (lane == 0 && status) ph_flag(status, PH_ERR_TIMEOUT);
           break;
         }
@@ -207,7 +219,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan(const int32_t* in, int32_t* out
     }
     if (lane == 0) {
       __threadfence();
-      st[tile] = kScanInc | (unsigned long long)(prefix + tot);
+      if (publish) st[tile] = kScanInc | (unsigned long long)(prefix + tot);
       s_prefix = prefix;
       if (tile == last && d_total) *d_total = prefix + tot;
     }
@@ -250,9 +262,11 @@ ph_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* d_
   }
   if (e == cudaSuccess) {
     KernelTimer kt("k_scan", s, 2);
+    const bool withhold = g_scan_withhold.load(std::memory_order_relaxed) != 0;
     k_scan<<<(unsigned)ntiles, SCAN_T, 0, s>>>(in, out, n, d_len, len_add, d_total, state,
                                                reinterpret_cast<unsigned*>(state + ntiles), status, mates,
-                                               nmates);
+                                               nmates, withhold ? kScanTestSpinLimit : kScanSpinLimit,
+                                               withhold ? 1 : -1);
     e = launched();
     kt.stop();
   }
@@ -399,7 +413,86 @@ __global__ void k_half_sqrt(const double* __restrict__ x, int64_t n, double* __r
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = ph::half_sqrt(x[i]);
 }
+
+// FP64 pipe throughput probe: every thread runs kPeakChains independent
+// chains x <- x m + b (one DFMA each), so the pipe never waits on a result;
+// m and b come in as arguments (nothing folds at compile time) and keep the
+// iterates bounded (|m| < 1).  Each thread stores its sum, so no chain is
+// dead code.
+constexpr int kPeakChains = 16;
+
+__global__ void __launch_bounds__(256) k_dfma_peak(int64_t iters, double m, double b, double* __restrict__ sink) {
+  double x[kPeakChains];
+#pragma unroll
+  for (int j = 0; j < kPeakChains; ++j) x[j] = (double)(threadIdx.x + j);
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < kPeakChains; ++j) x[j] = fma(x[j], m, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < kPeakChains; ++j) s += x[j];
+  sink[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = s;
+}
 }  // namespace
+
+extern "C" ph_status ph_test_fail_alloc(int64_t after) {
+  ph::g_fail_alloc_after.store(after < 0 ? -1 : after);
+  return PH_OK;
+}
+
+extern "C" ph_status ph_test_scan_withhold(int on) {
+  ph::g_scan_withhold.store(on ? 1 : 0);
+  return PH_OK;
+}
+
+extern "C" ph_status ph_pool_in_use(int64_t* bytes) {
+  if (!bytes) return PH_ERR_ARG;
+  *bytes = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  cudaMemPool_t pool;
+  if (e == cudaSuccess) e = ph::pool_for(dev, &pool);
+  uint64_t used = 0;
+  if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+  if (e != cudaSuccess) return ph::cuda_status(e, "ph_pool_in_use");
+  *bytes = (int64_t)used;
+  return PH_OK;
+}
+
+extern "C" ph_status ph_fp64_peak(int64_t iters, double* ops_per_s, double* ms_out, void* stream) {
+  if (iters <= 0 || !ops_per_s) return PH_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return ph::cuda_status(e, "ph_fp64_peak");
+  constexpr int kThreadsPeak = 256, kBlocksPerSm = 8;
+  const unsigned grid = (unsigned)(sms * kBlocksPerSm);
+  double* sink = nullptr;
+  e = ph::alloc(&sink, (size_t)grid * kThreadsPeak, s);
+  if (e != cudaSuccess) return ph::cuda_status(e, "ph_fp64_peak alloc");
+  cudaEvent_t a = nullptr, b = nullptr;
+  e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaEventRecord(a, s);
+  if (e == cudaSuccess) {
+    k_dfma_peak<<<grid, kThreadsPeak, 0, s>>>(iters, 0.999999, 1e-3, sink);
+    e = ph::launched();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  ph::free_async(sink, s);
+  if (e != cudaSuccess) return ph::cuda_status(e, "ph_fp64_peak");
+  const double ops = (double)grid * kThreadsPeak * kPeakChains * (double)iters;
+  *ops_per_s = ops / (t * 1e-3);
+  if (ms_out) *ms_out = t;
+  return PH_OK;
+}
 
 extern "C" ph_status ph_rcp(const double* x, int64_t n, double* y, void* stream) {
   if (n < 0 || (n > 0 && (!x || !y))) return PH_ERR_ARG;

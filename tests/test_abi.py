@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "ph.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(ph_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(ph_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")

@@ -51,6 +51,12 @@ def test_reference_arm_other_ranks_exit():
     assert r.stdout.strip() == ""
 
 
+def bench_cores():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench.host_cores()
+
+
 def test_reference_arm_json_line():
     """Rank 0 of the oracle (reference) arm prints one JSON line with the
     contract's keys: the native arm's metric and config, the oracle's own
@@ -60,7 +66,7 @@ def test_reference_arm_json_line():
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         env.pop(k, None)
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "3", "--ref-step-s", "0.2"],
+                        "--warmup", "3", "--ref-step-s", "0.2", "--workload", "lognormal_3m"],
                        env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
@@ -71,5 +77,5 @@ def test_reference_arm_json_line():
     assert d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1 and d["value"] > 0
     assert d["config"]["workload"] == "lognormal_3m" and d["config"]["nE"] == 3359232
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == bench_cores() and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "tets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -205,6 +205,32 @@ def test_solve_and_recover_parity(ph, name):
     g["mesh"].close()
 
 
+@pytest.mark.parametrize("name", ["jitter_checker_small", "lognormal_small"])
+def test_refined_solve_parity(ph, name):
+    """The whole path with solves refined to fp64 accuracy on both sides:
+    GPU assembly + ph_solve_refined against oracle assembly + the oracle's
+    refined direct solve.  The two assemblies differ in the last bits of H and
+    rhs, so the bar is 1e-9, or 10x the system's measured intrinsic
+    sensitivity (one-ulp perturbations, oracle) where that is above 1e-9;
+    both numbers are printed."""
+    p = make_case(name)
+    g = run_gpu(ph, p)
+    o = run_oracle(p, f=g["f"], uD=g["uD"], gN=g["gN"])
+    rowptr, colind = o["csr"]["rowptr"], o["csr"]["colind"]
+    lam_o, _, _ = oracle.solve_refined(rowptr, colind, o["values"], o["rhs"])
+    mesh = g["mesh"]
+    P = ph.Schwarz(mesh, cu(g["values"], torch.float64))
+    lam_g, steps, it, corr, _ = ph.solve_refined(mesh, cu(g["values"], torch.float64), cu(g["rhs"], torch.float64),
+                                                 P, tol=1e-15)
+    P.close()
+    err = np.linalg.norm(lam_g.cpu().numpy() - lam_o) / np.linalg.norm(lam_o)
+    sens = oracle.ulp_sensitivity(rowptr, colind, o["values"], o["rhs"], trials=2)
+    tol = SOLVE_RTOL if sens <= SOLVE_RTOL else 10 * sens
+    print(f"{name}: Lambda error {err:.3e}, intrinsic sensitivity {sens:.3e}, bar {tol:.3e}")
+    assert err <= tol
+    mesh.close()
+
+
 def test_table4_rates_from_gpu(ph):
     """The GPU pipeline reproduces the oracle's convergence behaviour (Table 4)."""
     from tests.test_oracle_system import error_norms
