@@ -233,11 +233,11 @@ def gpu_arm(args, rank, world, local_rank):
     a_h = torch.from_numpy(np.ascontiguousarray(p.a)).pin_memory()
     coord_d, tet_d, a_d = coord_h.to(dev), tet_h.to(dev), a_h.to(dev)
 
-    # face data at the face centroids (input preparation, untimed)
-    mesh = ph.Mesh(coord_d, tet_d)
-    info = dict(mesh.info)
-    cen = mesh.faces()["face_centroid"].cpu().numpy()
-    mesh.close()
+    # counts and face centroids from the host arrays alone (the query a
+    # host-only caller makes), face data at the centroids (input
+    # preparation, untimed)
+    info, cen = ph.ph_host_mesh_query(coord_h, tet_h)
+    cen = cen.numpy()
     f_h = torch.from_numpy(np.asarray(p.f(cen), np.float64)).pin_memory()
     lam_h = torch.from_numpy(np.random.default_rng(7).standard_normal(info["L"])).pin_memory()
     f_d, lam_d = f_h.to(dev), lam_h.to(dev)

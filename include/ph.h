@@ -418,8 +418,9 @@ int64_t ph_launch_count(void);
  * recovered).  Page-locked host buffers give full-speed, asynchronous copies;
  * pageable ones work but are staged.
  *   coord [nC*3], tet [nE*4], neumann [nN*3] or NULL: as ph_mesh_create.
- *   nF, L, nnz: the counts of the mesh these tets build (ph_mesh_info of an
- *     earlier build); they size the face data and the outputs, and a mismatch
+ *   nF, L, nnz: the counts of the mesh these tets build (ph_host_mesh_query
+ *     gives them from host arrays, with the face centroids the face data are
+ *     taken at); they size the face data and the outputs, and a mismatch
  *     with the build gives PH_ERR_ARG.
  *   a [nE], c, f_face [nF], uD_face [nF] or NULL, gN_face [nF] or NULL: as
  *     ph_assemble.  lambda [L] or NULL (with u NULL): the face values for the
@@ -435,6 +436,25 @@ ph_status ph_assemble_host(const double* coord, int64_t nC, const int32_t* tet, 
                            const double* a, double c, const double* f_face, const double* uD_face,
                            const double* gN_face, const double* lambda, int32_t* rowptr, int32_t* colind,
                            double* values, double* rhs, double* u, void* stream);
+
+/*
+ * The counts, and optionally the face centroids, of the mesh that HOST arrays
+ * build: what a caller holding only host memory needs before
+ * ph_assemble_host (its nF, L, nnz size the outputs, and f, u_D, g are taken
+ * at the face centroids).  Uploads the mesh, builds it as ph_mesh_create
+ * does (Section 3.3), and releases it.
+ *   coord [nC*3], tet [nE*4], neumann [nN*3] or NULL: host arrays, as in
+ *     ph_assemble_host.
+ *   info (host) out: the counts (ph_mesh_info).
+ *   face_centroid (host, may be NULL) out: nF rows of (P_x + P_y + P_z)/3 in
+ *     face order (ph_mesh_faces); centroid_capacity rows are available, and
+ *     4 nE + nN always suffice.  Fewer than nF gives PH_ERR_ARG.
+ * Device memory comes from the library's pool and is released before the
+ * call returns; synchronises `stream`.  Errors as ph_mesh_create.
+ */
+ph_status ph_host_mesh_query(const double* coord, int64_t nC, const int32_t* tet, int64_t nE, const int32_t* neumann,
+                             int64_t nN, ph_info* info, double* face_centroid, int64_t centroid_capacity,
+                             void* stream);
 
 /*
  * Kernel timing, off by default.  `on` is a mask: bit 0 times k_assemble,

@@ -35,7 +35,7 @@ EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces",
            "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy", "ph_rcp", "ph_half_sqrt", "ph_timing_enable",
            "ph_kernel_time", "ph_assemble_host", "ph_schwarz_create", "ph_schwarz_destroy",
            "ph_solve_pcg_schwarz", "ph_fp64_peak", "ph_test_fail_alloc", "ph_test_scan_withhold",
-           "ph_pool_in_use", "ph_solve_refined", "ph_mesh_create_batch")
+           "ph_pool_in_use", "ph_solve_refined", "ph_mesh_create_batch", "ph_host_mesh_query")
 
 
 class PHError(RuntimeError):
@@ -68,6 +68,7 @@ def load(path: str | None = None):
     sig = {
         "ph_mesh_create": [P, I64, P, I64, P, I64, P, ctypes.POINTER(P)],
         "ph_mesh_create_batch": [I32, P, P, P, P, P, P, P, P],
+        "ph_host_mesh_query": [P, I64, P, I64, P, I64, ctypes.POINTER(ph_info), P, I64, P],
         "ph_mesh_destroy": [P, P],
         "ph_mesh_info": [P, ctypes.POINTER(ph_info)],
         "ph_mesh_faces": [P, P, P, P, P, P, P, P, P],
@@ -440,6 +441,21 @@ def _hptr(t):
     if t.is_cuda or not t.is_contiguous():
         raise ValueError("expected a contiguous CPU tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def ph_host_mesh_query(coord, tet, neumann=None, centroids=True, stream=None):
+    """Counts (dict as Mesh.info) and, with centroids, the face centroids
+    (nF x 3 CPU tensor) of the mesh that host tensors build."""
+    nE = tet.shape[0]
+    nN = 0 if neumann is None else neumann.shape[0]
+    cap = 4 * nE + nN
+    cen = torch.empty((max(cap, 1), 3), dtype=torch.float64) if centroids else None
+    inf = ph_info()
+    _check(load().ph_host_mesh_query(_hptr(coord), coord.shape[0], _hptr(tet), nE, _hptr(neumann), nN,
+                                     ctypes.byref(inf), _hptr(cen), cap if centroids else 0, _stream(stream)),
+           "ph_host_mesh_query")
+    info = {f: int(getattr(inf, f)) for f, _ in ph_info._fields_}
+    return info, (cen[:info["nF"]] if centroids else None)
 
 
 def ph_assemble_host(coord, tet, a, c, f_face, counts, lam=None, uD_face=None, gN_face=None, neumann=None,

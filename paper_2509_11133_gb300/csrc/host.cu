@@ -155,3 +155,65 @@ done:
   release_streams(dev, up, down);  // idle: the caller's stream waited for both
   return st;
 }
+
+// Counts (and face centroids) of the mesh that host arrays build: the query a
+// caller with only host memory makes before ph_assemble_host, to size its
+// outputs and evaluate f, u_D, g at the face centroids.
+namespace {
+__global__ void k_centroids(const double* __restrict__ coord, const int32_t* __restrict__ face_vtx, int64_t nF,
+                            double* __restrict__ out) {
+  const int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (F >= nF) return;
+  const double* x = coord + 3 * (int64_t)face_vtx[3 * F];
+  const double* y = coord + 3 * (int64_t)face_vtx[3 * F + 1];
+  const double* z = coord + 3 * (int64_t)face_vtx[3 * F + 2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) out[3 * F + d] = (x[d] + y[d] + z[d]) / 3.0;
+}
+}  // namespace
+
+extern "C" ph_status ph_host_mesh_query(const double* coord, int64_t nC, const int32_t* tet, int64_t nE,
+                                        const int32_t* neumann, int64_t nN, ph_info* info, double* face_centroid,
+                                        int64_t centroid_capacity, void* stream) {
+  if (!info || nC < 0 || nE < 0 || nN < 0 || centroid_capacity < 0) return PH_ERR_ARG;
+  if ((nC > 0 && !coord) || (nE > 0 && !tet) || (nN > 0 && !neumann)) return PH_ERR_ARG;
+  if (4 * nE + nN >= ((int64_t)1 << 31) - 1) return PH_ERR_OVERFLOW;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* d_coord = nullptr;
+  int32_t *d_tet = nullptr, *d_neu = nullptr;
+  double* d_cen = nullptr;
+  ph_mesh* m = nullptr;
+  ph_status st = PH_OK;
+  cudaError_t e = alloc(&d_coord, (size_t)(3 * nC), s);
+  if (e == cudaSuccess) e = alloc(&d_tet, (size_t)(4 * nE), s);
+  if (e == cudaSuccess && nN > 0) e = alloc(&d_neu, (size_t)(3 * nN), s);
+  if (e == cudaSuccess) e = upload(d_coord, coord, 3 * nC, s);
+  if (e == cudaSuccess) e = upload(d_tet, tet, 4 * nE, s);
+  if (e == cudaSuccess) e = upload(d_neu, neumann, 3 * nN, s);
+  if (e != cudaSuccess) {
+    st = cuda_status(e, "ph_host_mesh_query");
+  } else {
+    st = ph_mesh_create(d_coord, nC, d_tet, nE, d_neu, nN, s, &m);  // blocks the host once
+  }
+  if (st == PH_OK) st = ph_mesh_info(m, info);
+  if (st == PH_OK && face_centroid && m->nF > 0) {
+    if (centroid_capacity < m->nF) {
+      set_error_text("ph_host_mesh_query: face_centroid holds fewer than nF rows");
+      st = PH_ERR_ARG;
+    } else {
+      e = alloc(&d_cen, (size_t)(3 * m->nF), s);
+      if (e == cudaSuccess) {
+        k_centroids<<<grid_for(m->nF), kThreads, 0, s>>>(m->coord, m->face_vtx, m->nF, d_cen);
+        e = launched();
+      }
+      if (e == cudaSuccess) e = download(face_centroid, d_cen, 3 * m->nF, s);
+      if (e != cudaSuccess) st = cuda_status(e, "ph_host_mesh_query");
+    }
+  }
+  if (m) ph_mesh_destroy(m, s);
+  for (void* p : {(void*)d_coord, (void*)d_tet, (void*)d_neu, (void*)d_cen}) free_async(p, s);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess && st == PH_OK) st = cuda_status(e, "ph_host_mesh_query");
+  return st;
+}
+

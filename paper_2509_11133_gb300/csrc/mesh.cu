@@ -820,24 +820,29 @@ struct UnionSources {
   const int32_t* nb;   // problem's Neumann triples or null
 };
 
-// union tets and Neumann triples: problem p's ids shifted by voff[p]
+// union tets and Neumann triples: problem p's ids shifted by voff[p].  An id
+// outside [0, nC_p) would land on another problem's vertex, so it becomes -1,
+// which the union build rejects (PH_ERR_ARG).
+__device__ __forceinline__ int shift_vertex(int x, int v, int nv) { return (x >= 0 && x < nv) ? x + v : -1; }
+
 __global__ void k_union_inputs(const UnionSources* __restrict__ src, const int64_t* __restrict__ toff,
                                const int64_t* __restrict__ noff, const int64_t* __restrict__ voff, int32_t n,
                                int64_t nE, int64_t nN, int4* __restrict__ tet_u, int32_t* __restrict__ nb_u) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < nE) {
     const int p = problem_of(toff, n, i);
-    const int v = (int)voff[p];
+    const int v = (int)voff[p], nv = (int)(voff[p + 1] - voff[p]);
     const int4 t = reinterpret_cast<const int4*>(src[p].tet)[i - toff[p]];
-    tet_u[i] = make_int4(t.x + v, t.y + v, t.z + v, t.w + v);
+    tet_u[i] = make_int4(shift_vertex(t.x, v, nv), shift_vertex(t.y, v, nv), shift_vertex(t.z, v, nv),
+                         shift_vertex(t.w, v, nv));
   } else if (i < nE + nN) {
     const int64_t j = i - nE;
     const int p = problem_of(noff, n, j);
-    const int v = (int)voff[p];
+    const int v = (int)voff[p], nv = (int)(voff[p + 1] - voff[p]);
     const int64_t k = j - noff[p];
-    nb_u[3 * j] = src[p].nb[3 * k] + v;
-    nb_u[3 * j + 1] = src[p].nb[3 * k + 1] + v;
-    nb_u[3 * j + 2] = src[p].nb[3 * k + 2] + v;
+    nb_u[3 * j] = shift_vertex(src[p].nb[3 * k], v, nv);
+    nb_u[3 * j + 1] = shift_vertex(src[p].nb[3 * k + 1], v, nv);
+    nb_u[3 * j + 2] = shift_vertex(src[p].nb[3 * k + 2], v, nv);
   }
 }
 

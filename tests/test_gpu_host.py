@@ -1,7 +1,9 @@
 """ph_assemble_host (the whole path from and to host buffers, copies
 overlapped with the kernels) against the same steps through the device entry
 points: bit-identical outputs, pinned and pageable buffers, with and without
-Neumann and Dirichlet data, and the count check."""
+Neumann and Dirichlet data, and the count check; and the cold host path: the
+counts and face centroids from ph_host_mesh_query alone, with no device
+tensor in the caller's hands."""
 import numpy as np
 import pytest
 
@@ -81,3 +83,32 @@ def test_host_path_full_size(ph):
                               lam=pin(data["lam"]))
     for k in ("rowptr", "colind", "values", "rhs", "u"):
         assert torch.equal(out[k], ref[k]), k
+
+
+@pytest.mark.parametrize("case", ["lognormal_small", "paper_mixed2"])
+def test_cold_host_path(ph, case):
+    if case == "paper_mixed2":
+        p = meshgen.problem("paper_mixed", 2)
+    else:
+        coord, tet = meshgen.kuhn_cube(3)
+        coord, tet, _ = meshgen.refined(coord, tet, 2)
+        p = meshgen.Problem(case, coord, tet, meshgen.lognormal_field(tet.shape[0], 2), 0.1,
+                            lambda x: meshgen.sin_source(x))
+    data, ref, counts = device_path(ph, p)
+    h = lambda x: None if x is None else torch.from_numpy(np.ascontiguousarray(x))
+    neu = h(p.neumann.astype(np.int32)) if p.neumann.size else None
+    info, cen = ph.ph_host_mesh_query(h(p.coord), h(p.tet.astype(np.int32)), neu)
+    assert (info["nF"], info["L"], info["nnz"]) == counts
+    cen = cen.numpy()
+    f = np.asarray(p.f(cen), np.float64)
+    assert np.array_equal(f, data["f"])  # the same centroids as the device build's
+    uD = None if p.uD is None else np.asarray(p.uD(cen), np.float64)
+    gN = None if p.gN is None else np.asarray(p.gN(cen), np.float64)
+    out = ph.ph_assemble_host(h(p.coord), h(p.tet.astype(np.int32)), h(p.a), p.c, h(f),
+                              (info["nF"], info["L"], info["nnz"]), lam=h(data["lam"]), uD_face=h(uD), gN_face=h(gN),
+                              neumann=neu)
+    for k in ("rowptr", "colind", "values", "rhs", "u"):
+        assert torch.equal(out[k], ref[k]), k
+    # counts only, and a centroid buffer that is too small
+    info2, none = ph.ph_host_mesh_query(h(p.coord), h(p.tet.astype(np.int32)), neu, centroids=False)
+    assert info2 == info and none is None
