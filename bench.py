@@ -85,25 +85,25 @@ TIMED_KERNELS = ("k_assemble", "zero_values", "k_recover_factored")
 # mesh-build kernels, timed in a separate short loop (their timers add host
 # work between the build's launches)
 BUILD_KERNELS = ("k_face_count", "k_face_fill", "k_face_match", "k_face_emit", "k_row_fill", "k_scan")
-# sources that k_assemble is compiled from
-ASSEMBLE_SOURCES = ("assemble.cu", "element.cuh", "fp64.cuh")
+# sources that k_assemble (both variants) is compiled from
+ASSEMBLE_SOURCES = ("assemble.cu", "element.cuh", "fp64.cuh", "dw.cuh")
 
 
-def assemble_sources_sha256():
+def assemble_sources_sha256(sources=ASSEMBLE_SOURCES):
     h = hashlib.sha256()
-    for name in ASSEMBLE_SOURCES:
+    for name in sources:
         with open(os.path.join(ROOT, "paper_2509_11133_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def profile_figures():
-    """Per-element figures of the committed ncu capture of k_assemble (taken
+def profile_figures(kernel="k_assemble"):
+    """Per-element figures of the committed ncu capture of a kernel (taken
     on a smaller mesh of the lognormal recipe; the kernel's work and traffic
     per element do not depend on the mesh size): DRAM bytes and FP64
     instructions per element.  Empty when the kernel's sources changed after
     the counters were taken."""
-    prof = os.path.join(ROOT, "profiles", "k_assemble_lognormal_1m.txt")
+    prof = os.path.join(ROOT, "profiles", f"{kernel}_lognormal_1m.txt")
     try:
         kv = {}
         for line in open(prof):
@@ -112,10 +112,10 @@ def profile_figures():
                 kv[k.strip()] = v.strip()
     except OSError:
         return {}
-    if kv.get("sources_sha256") != assemble_sources_sha256():
+    if kv.get("sources_sha256") != assemble_sources_sha256(tuple(kv.get("sources", "").split())):
         return {}
     out = {}
-    for key in ("dram_bytes_per_tet", "fp64_inst_per_tet"):
+    for key in ("dram_bytes_per_tet", "fp64_inst_per_tet", "fp32_inst_per_tet"):
         try:
             out[key] = float(kv[key])
         except (KeyError, ValueError):
@@ -304,6 +304,35 @@ def gpu_arm(args, rank, world, local_rank):
     for name in BUILD_KERNELS:
         ms, n = ph.ph_kernel_time(name, reset=True)
         build_kern[name] = ms / 5 if n else float("nan")  # per build (k_scan: all scans of one build)
+    # the precision variant: the same step with the condensation kernel in
+    # double-word arithmetic (ph_assemble_dw), its own timed loop
+    variant = None
+    if not args.no_variant:
+        def step_dw(ev=None):
+            if ev is not None:
+                ev[0].record(stream)
+            m = ph.Mesh(coord_d, tet_d)
+            m.assemble(a_d, p.c, f_d, values=values, rhs=rhs, factor=factor, variant="dw")
+            m.recover_factored(factor, p.c, f_d, lam_d, u=u)
+            if ev is not None:
+                ev[1].record(stream)
+            m.close()
+
+        for _ in range(args.warmup):
+            step_dw()
+            flush.zero_()
+        torch.cuda.synchronize()
+        evd = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+        ph.ph_kernel_time("k_assemble_dw", reset=True)
+        ph.ph_timing_enable(True)
+        for i in range(args.steps):
+            step_dw(evd[i])
+            flush.zero_()
+        torch.cuda.synchronize()
+        ph.ph_timing_enable(False)
+        ms, n = ph.ph_kernel_time("k_assemble_dw", reset=True)
+        variant = {"step_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in evd])),
+                   "k_assemble_dw_ms": ms / n if n else float("nan")}
     # the FP64 pipe's throughput on this GPU, measured now, under the same
     # clock sampling as the timed steps: best of 3 probe launches
     ph.ph_fp64_peak(FP64_PEAK_ITERS)
@@ -442,6 +471,9 @@ def gpu_arm(args, rank, world, local_rank):
         "clocks": clk,
         "setup": {"host_mesh_generation_s": gen_s},
     }
+    if variant is not None:
+        line["variant_dw"] = variant_report(variant, nE, p.nC, nF, world, fp64_peak_gops, hbm_peak, ms_per_step,
+                                            k_asm)
     if not args.no_extras:
         line["batched"] = batched_section(ph, dev, steps=max(3, args.steps // 10), warmup=3)
         line["adjoint"] = adjoint_section(ph, dev)
@@ -450,35 +482,98 @@ def gpu_arm(args, rank, world, local_rank):
     return line
 
 
+def variant_report(v, nE, nC, nF, world, fp64_peak_gops, hbm_peak, f64_step_ms, f64_k_asm_ms):
+    """The precision variant's line: the step with ph_assemble_dw and its
+    condensation kernel against the FP64 and HBM rooflines (per-element
+    instruction and traffic figures from the kernel's committed ncu capture
+    when it matches the sources)."""
+    k_s = v["k_assemble_dw_ms"] * 1e-3
+    prof = profile_figures("k_assemble_dw")
+    bpt = assemble_bytes_per_tet(nE, nC, nF)
+    out = {
+        "what": "ph_assemble_dw: the condensation kernel (the 3x3 algebra of A^-1) in double-word arithmetic "
+                "(float pairs, ~48 bits) on the FP32 pipe; leading terms, |det|, |F| and every sum of H and rhs "
+                "in fp64; same outputs as ph_assemble within 1e-13 (tested against the oracle at 1e-12)",
+        "dtype": "f64 + f32x2 (double-word) condensation kernel",
+        "value": whole_job_rate(nE, world, v["step_ms"]), "unit": UNIT, "ms_per_step": v["step_ms"],
+        "speedup_step_vs_f64": f64_step_ms / v["step_ms"],
+        "k_assemble_dw_ms": v["k_assemble_dw_ms"], "speedup_kernel_vs_f64": f64_k_asm_ms / v["k_assemble_dw_ms"],
+        "roofline_hbm": {"achieved": bpt * nE / k_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": bpt * nE / k_s / 1e9 / hbm_peak, "bytes_per_tet": bpt,
+                         "traffic": prof["dram_bytes_per_tet"] * nE if "dram_bytes_per_tet" in prof else None},
+    }
+    if "fp64_inst_per_tet" in prof:
+        g = prof["fp64_inst_per_tet"] * nE / k_s / 1e9
+        out["roofline_fp64"] = {"achieved": g, "peak": fp64_peak_gops, "unit": "G FP64-op/s",
+                                "frac": g / fp64_peak_gops, "ops_per_tet": prof["fp64_inst_per_tet"],
+                                "ops_source": "ncu FP64 instructions (DFMA+DADD+DMUL) per element"}
+    if "fp32_inst_per_tet" in prof:
+        out["fp32_inst_per_tet"] = prof["fp32_inst_per_tet"]
+    return out
+
+
 # ---------------------------------------------------------------------------
 # batched workload: 256 problems, Kuhn m_i^3 cubes refined once, m_i from
 # sizes log-uniform in [1e4, 5e5] elements (seed 4), each its own lognormal a
 # ---------------------------------------------------------------------------
 def batched_section(ph, dev, steps, warmup):
+    """The batched workload: 256 problems, each its own mesh (Kuhn m_i^3 cube
+    refined once) and lognormal field.  Mesh builds: 256 ph_mesh_create calls
+    against one ph_mesh_create_batch.  Numeric phase (assembly with the
+    element factor and recovery from a seeded Lambda): one captured graph of
+    three persistent launches against 256 sequential plain call pairs."""
     import torch
     rng = np.random.Generator(np.random.PCG64(4))
     sizes = np.exp(rng.uniform(np.log(1e4), np.log(5e5), 256))
     ms = np.clip(np.round((sizes / 72.0) ** (1.0 / 3.0)), 6, 19).astype(int)
-    cache = {}
+    inputs = {}
+    for m in sorted(set(ms.tolist())):
+        coord, tet = meshgen.kuhn_cube(int(m))
+        coord, tet, _ = meshgen.refined(coord, tet, 1)
+        inputs[m] = (torch.as_tensor(coord, device=dev), torch.as_tensor(tet, device=dev))
+    coords = [inputs[m][0] for m in ms]
+    tets = [inputs[m][1] for m in ms]
+
+    def build_separate():
+        out = [ph.Mesh(c, t) for c, t in zip(coords, tets)]
+        torch.cuda.synchronize()
+        return out
+
+    def build_batched():
+        out = ph.create_meshes(coords, tets)
+        torch.cuda.synchronize()
+        return out
+
+    build_ms = {}
+    for name, fn in (("separate_calls", build_separate), ("one_batched_call", build_batched)):
+        best = float("inf")
+        for _ in range(3):
+            t0 = time.perf_counter()
+            built = fn()
+            best = min(best, (time.perf_counter() - t0) * 1e3)
+            if name == "separate_calls" or _ < 2:  # keep the last batched build
+                for mm in built:
+                    mm.close()
+        build_ms[name] = best
+    meshes = built  # the batched build's meshes
+    fcache = {}
     probs = []
-    for i, m in enumerate(ms):
-        if m not in cache:
-            coord, tet = meshgen.kuhn_cube(int(m))
-            coord, tet, _ = meshgen.refined(coord, tet, 1)
-            mesh = ph.Mesh(torch.as_tensor(coord, device=dev), torch.as_tensor(tet, device=dev))
+    for i, (m, mesh) in enumerate(zip(ms, meshes)):
+        if m not in fcache:
             cen = mesh.faces()["face_centroid"].cpu().numpy()
-            f = torch.as_tensor(np.asarray(meshgen.sin_source(cen), np.float64), device=dev)
-            cache[m] = (mesh, f)
-        mesh, f = cache[m]
-        a = torch.as_tensor(meshgen.lognormal_field(mesh.nE, 4000 + i), device=dev)
-        probs.append(dict(mesh=mesh, f=f, a=a,
+            fcache[m] = torch.as_tensor(np.asarray(meshgen.sin_source(cen), np.float64), device=dev)
+        probs.append(dict(mesh=mesh, f=fcache[m], a=torch.as_tensor(meshgen.lognormal_field(mesh.nE, 4000 + i),
+                                                                     device=dev),
                           values=torch.empty(mesh.nnz, dtype=torch.float64, device=dev),
                           rhs=torch.empty(mesh.L, dtype=torch.float64, device=dev),
-                          factor=torch.empty((mesh.nE, 10), dtype=torch.float64, device=dev)))
+                          factor=torch.empty((mesh.nE, 10), dtype=torch.float64, device=dev),
+                          lam=torch.as_tensor(np.random.default_rng(70 + i).standard_normal(mesh.L), device=dev),
+                          u=torch.empty((mesh.nE, 4), dtype=torch.float64, device=dev)))
     total = sum(p["mesh"].nE for p in probs)
     batch = ph.Batch([p["mesh"] for p in probs])
     batch.bind([p["a"] for p in probs], [0.1] * len(probs), [p["f"] for p in probs], [p["values"] for p in probs],
                [p["rhs"] for p in probs], factor=[p["factor"] for p in probs])
+    batch.bind_recovery([p["lam"] for p in probs], [p["u"] for p in probs])
     tune_ms = batch.autotune(reps=2)
     cfg = dict(batch.get_config(), best_ms=tune_ms)
     stream = torch.cuda.current_stream()
@@ -502,13 +597,18 @@ def batched_section(ph, dev, steps, warmup):
     def plain():
         for p in probs:
             p["mesh"].assemble(p["a"], 0.1, p["f"], values=p["values"], rhs=p["rhs"], factor=p["factor"])
+            p["mesh"].recover_factored(p["factor"], 0.1, p["f"], p["lam"], u=p["u"])
 
     n0 = ph.ph_launch_count()
     plain_ms = timed(plain)
     launches_plain = (ph.ph_launch_count() - n0) / (steps + warmup)
     batch.close()
+    for p in probs:
+        p["mesh"].close()
     return {
-        "problems": len(probs), "tets": int(total), "distinct_meshes": len(cache),
+        "problems": len(probs), "tets": int(total), "distinct_mesh_shapes": len(inputs),
+        "step": "assembly and condensation with the element factor + recovery from a seeded Lambda",
+        "mesh_build_ms": build_ms, "mesh_build_speedup": build_ms["separate_calls"] / build_ms["one_batched_call"],
         "batched_graph_ms": graph_ms, "batched_tets_per_s": total / (graph_ms * 1e-3),
         "plain_sequential_ms": plain_ms, "plain_sequential_tets_per_s": total / (plain_ms * 1e-3),
         "speedup_vs_sequential": plain_ms / graph_ms, "autotuned": cfg,
@@ -671,11 +771,12 @@ def profile_pcg(iters):
     return 0
 
 
-def profile_kernels(workload, reps):
-    """Profiler target for the element kernels besides k_assemble: on the
-    given workload, `reps` rounds of assembly with the element factor,
-    recovery from a seeded Lambda, the misfit, the adjoint right-hand side and
-    the adjoint gradient from a seeded q (no solves, so few launches)."""
+def profile_kernels(workload, reps, variant="f64"):
+    """Profiler target for the element kernels: on the given workload, `reps`
+    rounds of assembly with the element factor (ph_assemble, or
+    ph_assemble_dw for variant "dw"), recovery from a seeded Lambda, the
+    misfit, the adjoint right-hand side and the adjoint gradient from a seeded
+    q (no solves, so few launches)."""
     import torch
     import paper_2509_11133_gb300 as ph
     from paper_2509_11133_gb300 import build
@@ -692,14 +793,14 @@ def profile_kernels(workload, reps):
     q = torch.as_tensor(rng.standard_normal(mesh.L), device=dev)
     u_obs = torch.as_tensor(rng.standard_normal((mesh.nE, 4)), device=dev)
     for _ in range(reps):
-        values, rhs, factor = mesh.assemble(a, p.c, f, factor=True)
+        values, rhs, factor = mesh.assemble(a, p.c, f, factor=True, variant=variant)
         u = mesh.recover_factored(factor, p.c, f, lam)
         mesh.misfit(u, u_obs)
         mesh.adjoint_rhs(factor, p.c, u, u_obs)
         mesh.adjoint_grad(a, factor, p.c, u, u_obs, q)
     torch.cuda.synchronize()
     mesh.check()
-    print(json.dumps({"profile_kernels": {"workload": workload, "nE": mesh.nE, "reps": reps}}))
+    print(json.dumps({"profile_kernels": {"workload": workload, "nE": mesh.nE, "reps": reps, "variant": variant}}))
     mesh.close()
     return 0
 
@@ -778,6 +879,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiler runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint sections")
+    ap.add_argument("--no-variant", action="store_true", help="skip the double-word assembly variant's timed loop")
+    ap.add_argument("--variant", default="f64", choices=["f64", "dw"],
+                    help="assembly used by --profile-kernels")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=3.0)
@@ -795,7 +899,7 @@ def main():
     if args.profile_pcg > 0:
         return profile_pcg(args.profile_pcg)
     if args.profile_kernels > 0:
-        return profile_kernels(args.workload, args.profile_kernels)
+        return profile_kernels(args.workload, args.profile_kernels, args.variant)
     if args.impl == "reference":
         if rank != 0:
             return 0

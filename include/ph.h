@@ -185,6 +185,22 @@ ph_status ph_assemble(const ph_mesh* mesh, const double* a, double c, const doub
                       double* factor, void* stream);
 
 /*
+ * ph_assemble with the element condensation kernel (the 3x3 algebra behind
+ * A(T)^-1 on the complement of the constants, Eq. schur) evaluated in
+ * double-word arithmetic on the FP32 pipe: pairs of floats carrying ~48
+ * significant bits (Dekker's exact transforms; the error bounds of Joldes,
+ * Muller and Popescu 2017), with the leading term d d'/(c|T|), |det|, |F|
+ * and every sum of H and rhs kept in fp64.  A precision variant, not in the
+ * paper: same arguments, outputs and error behaviour as ph_assemble, results
+ * within ~1e-14 relative of it (both within 1e-12 of the exact values).  An
+ * element whose reaction term dominates (c h^2 comparable to a) or whose
+ * data leave the exponent range of the float pairs is condensed in fp64.
+ */
+ph_status ph_assemble_dw(const ph_mesh* mesh, const double* a, double c, const double* f_face,
+                         const double* uD_face, const double* gN_face, double* values, double* rhs, double* factor,
+                         void* stream);
+
+/*
  * Element recovery (Algorithm 1 second loop): U(T) = A(T)^-1 (B(T) + C(T)'
  * Lambda_T), Lambda_T(k) = lambda[l(F_k)] and 0 on Neumann faces.
  *   lambda [L] float64, u [nE*4] float64 out (values of u_h at the 4 vertices
@@ -288,6 +304,17 @@ ph_status ph_batch_autotune(ph_batch* batch, int32_t reps, float* best_ms, void*
 ph_status ph_batch_set_config(ph_batch* batch, int32_t tile, int32_t threads, int32_t blocks_per_sm, void* stream);
 ph_status ph_batch_get_config(const ph_batch* batch, int32_t* tile, int32_t* threads, int32_t* blocks_per_sm);
 ph_status ph_batch_graph_launch(ph_batch* batch, void* stream);
+/*
+ * ph_batch_bind_recovery: add element recovery from the element factor
+ * (Algorithm 1, second loop, as ph_recover_factored) to the batch: host
+ * arrays of n DEVICE pointers lambda[i] [L_i] and u[i] [nE_i*4]; every
+ * problem must have been bound with a factor.  ph_batch_assemble and the
+ * graph then run a third persistent kernel after the assembly, and each
+ * problem's u is bit-identical to ph_recover_factored on its factor.
+ * lambda = NULL removes the recovery.  Synchronises `stream`; the graph is
+ * rebuilt on its next launch when the recovery is added or removed.
+ */
+ph_status ph_batch_bind_recovery(ph_batch* batch, const double* const* lambda, double* const* u, void* stream);
 
 /*
  * Uniform refinement on the device (Section 3.4, Listing RedRefine): every

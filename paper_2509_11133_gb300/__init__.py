@@ -35,7 +35,8 @@ EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces",
            "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy", "ph_rcp", "ph_half_sqrt", "ph_timing_enable",
            "ph_kernel_time", "ph_assemble_host", "ph_schwarz_create", "ph_schwarz_destroy",
            "ph_solve_pcg_schwarz", "ph_fp64_peak", "ph_test_fail_alloc", "ph_test_scan_withhold",
-           "ph_pool_in_use", "ph_solve_refined", "ph_mesh_create_batch", "ph_host_mesh_query")
+           "ph_pool_in_use", "ph_solve_refined", "ph_mesh_create_batch", "ph_host_mesh_query",
+           "ph_assemble_dw", "ph_batch_bind_recovery")
 
 
 class PHError(RuntimeError):
@@ -74,6 +75,7 @@ def load(path: str | None = None):
         "ph_mesh_faces": [P, P, P, P, P, P, P, P, P],
         "ph_csr_pattern": [P, P, P, P],
         "ph_assemble": [P, P, D, P, P, P, P, P, P, P],
+        "ph_assemble_dw": [P, P, D, P, P, P, P, P, P, P],
         "ph_recover_factored": [P, P, D, P, P, P, P, P],
         "ph_recover": [P, P, D, P, P, P, P, P],
         "ph_solve_pcg": [I64, P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P],
@@ -91,6 +93,7 @@ def load(path: str | None = None):
         "ph_batch_set_config": [P, I32, I32, I32, P],
         "ph_batch_get_config": [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)],
         "ph_batch_graph_launch": [P, P],
+        "ph_batch_bind_recovery": [P, P, P, P],
         "ph_refine": [P, I64, P, I64, P, I64, P, ctypes.POINTER(P)],
         "ph_refined_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)],
         "ph_refined_copy": [P, P, P, P, P],
@@ -336,9 +339,11 @@ class Mesh:
         _check(load().ph_csr_pattern(self._h, _ptr(rowptr), _ptr(colind), _stream(stream)), "ph_csr_pattern")
         return rowptr, colind
 
-    def assemble(self, a, c, f_face, uD_face=None, gN_face=None, values=None, rhs=None, factor=None, stream=None):
+    def assemble(self, a, c, f_face, uD_face=None, gN_face=None, values=None, rhs=None, factor=None, stream=None,
+                 variant="f64"):
         """H values and rhs; with ``factor`` (nE*10 float64, or True to
-        allocate) also the element factor for recover_factored."""
+        allocate) also the element factor for recover_factored.  variant
+        "dw" runs ph_assemble_dw (condensation kernel in double-word)."""
         _need(a, torch.float64, self.nE, "a")
         _need(f_face, torch.float64, self.nF, "f_face")
         if uD_face is not None:
@@ -352,8 +357,11 @@ class Mesh:
             factor = self._empty((self.nE, 10), torch.float64)
         elif factor is not None:
             _need(factor, torch.float64, 10 * self.nE, "factor")
-        _check(load().ph_assemble(self._h, _ptr(a), float(c), _ptr(f_face), _ptr(uD_face), _ptr(gN_face),
-                                  _ptr(values), _ptr(rhs), _ptr(factor), _stream(stream)), "ph_assemble")
+        if variant not in ("f64", "dw"):
+            raise ValueError("variant: 'f64' or 'dw'")
+        fn = load().ph_assemble if variant == "f64" else load().ph_assemble_dw
+        _check(fn(self._h, _ptr(a), float(c), _ptr(f_face), _ptr(uD_face), _ptr(gN_face), _ptr(values), _ptr(rhs),
+                  _ptr(factor), _stream(stream)), "ph_assemble" if variant == "f64" else "ph_assemble_dw")
         if factor is not None:
             return values, rhs, factor
         return values, rhs
@@ -594,6 +602,20 @@ class Batch:
         _check(load().ph_batch_bind(self._h, arrs[0], cs, arrs[1], arrs[2], arrs[3], arrs[4], arrs[5], arrs[6],
                                     _stream(stream)), "ph_batch_bind")
         self._bound = (a, c, f_face, values, rhs, factor, uD_face, gN_face)
+
+    def bind_recovery(self, lam, u, stream=None):
+        """Recovery from the bound factors into u[i] (lists of CUDA tensors;
+        lam None removes it)."""
+        if lam is None:
+            _check(load().ph_batch_bind_recovery(self._h, None, None, _stream(stream)), "ph_batch_bind_recovery")
+            self._recovery = None
+            return
+        for m, l, uu in zip(self.meshes, lam, u):
+            _need(l, torch.float64, m.L, "lambda")
+            _need(uu, torch.float64, 4 * m.nE, "u")
+        _check(load().ph_batch_bind_recovery(self._h, _ptr_array(lam), _ptr_array(u), _stream(stream)),
+               "ph_batch_bind_recovery")
+        self._recovery = (lam, u)
 
     def assemble(self, stream=None):
         _check(load().ph_batch_assemble(self._h, _stream(stream)), "ph_batch_assemble")

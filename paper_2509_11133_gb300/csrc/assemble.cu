@@ -36,7 +36,7 @@ using namespace ph_elem;
 
 namespace {
 
-template <bool UD, bool GN, bool FAC>
+template <bool UD, bool GN, bool FAC, bool DW>
 __global__ void __launch_bounds__(128) k_assemble(int64_t nE, const double* __restrict__ geo,
                                                   const int4* __restrict__ tface, const int4* __restrict__ tmult,
                                                   const int4* __restrict__ tpos, const ushort4* __restrict__ trel,
@@ -47,36 +47,10 @@ __global__ void __launch_bounds__(128) k_assemble(int64_t nE, const double* __re
                                                   double* __restrict__ factor, unsigned* status) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nE) return;
-  assemble_element<UD, GN, FAC>(t, geo, tface, tmult, tpos, trel, face_area, a, c20, six_over_c, f_face, uD, gN,
-                                values, rhs, factor, status);
+  assemble_element<UD, GN, FAC, DW>(t, geo, tface, tmult, tpos, trel, face_area, a, c20, six_over_c, f_face, uD,
+                                    gN, values, rhs, factor, status);
 }
 
-__device__ __forceinline__ void store_u(double* __restrict__ u, int64_t t, const double U[4]) {
-  // vertex j holds U of the face opposite it: j = 0,1,2,3 <- k = 3,1,2,0
-  double2* out = reinterpret_cast<double2*>(u + 4 * t);
-  out[0] = make_double2(U[3], U[1]);
-  out[1] = make_double2(U[2], U[0]);
-}
-
-// z'_k = |T|/4 f(Ct_k) + |F_k| g(Ct_k) [Neumann] + d_k Lambda_k
-template <bool GN>
-__device__ __forceinline__ void recovery_load(double q4, int4 tf, int4 tm, const double* __restrict__ face_area,
-                                              const double* __restrict__ f_face, const double* __restrict__ gN,
-                                              const double* __restrict__ lambda, double z[4]) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int F = comp(tf, k) & PH_ID_MASK;
-    const int mk = comp(tm, k);
-    const double ar = __ldg(face_area + F);
-    double zk = q4 * __ldg(f_face + F);
-    if (mk == PH_NO_MULT) {
-      if (GN) zk = fma(ar, __ldg(gN + F), zk);
-    } else {
-      zk = fma(neg_if(ar, comp(tf, k) < 0), __ldg(lambda + (mk & PH_ID_MASK)), zk);
-    }
-    z[k] = zk;
-  }
-}
 
 template <bool GN>
 __global__ void __launch_bounds__(128) k_recover(int64_t nE, const double* __restrict__ geo,
@@ -121,24 +95,7 @@ __global__ void __launch_bounds__(128) k_recover_factored(int64_t nE, const doub
                                                           const double* __restrict__ lambda, double* __restrict__ u) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nE) return;
-  const double2 dr = __ldg(reinterpret_cast<const double2*>(geo + PH_GEO_STRIDE * t) + 7);  // (t22, |det|)
-  const double rdet = __ldg(geo + PH_GEO_STRIDE * t + 16);
-  double z[4];
-  recovery_load<GN>(dr.y * (1.0 / 24.0), __ldg(tface + t), __ldg(tmult + t), face_area, f_face, gN, lambda, z);
-  const double2* fp = reinterpret_cast<const double2*>(factor + 10 * t);
-  const double2 q0 = __ldg(fp), q1 = __ldg(fp + 1), q2 = __ldg(fp + 2), q3 = __ldg(fp + 3), q4 = __ldg(fp + 4);
-  const double Q[10] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y, q3.x, q3.y, q4.x, q4.y};
-  const double icT = rdet * six_over_c;
-  const double zs = icT * ((z[0] + z[1]) + (z[2] + z[3]));
-  double U[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    double e = 0.0;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) e = fma(Q[ut(k, m)], z[m], e);
-    U[k] = fma(-3.0, e, zs);  // U[o(k)] = z'sum/(c|T|) - 3 (Qf/9 z')_k
-  }
-  store_u(u, t, U);
+  recover_element_factored<GN>(t, geo, tface, tmult, face_area, factor, six_over_c, f_face, gN, lambda, u);
 }
 
 bool finite_pos(double x) { return x > 0.0 && x < INFINITY; }
@@ -147,9 +104,9 @@ bool finite_pos(double x) { return x > 0.0 && x < INFINITY; }
 
 using namespace ph;
 
-extern "C" ph_status ph_assemble(const ph_mesh* m, const double* a, double c, const double* f_face,
-                                 const double* uD_face, const double* gN_face, double* values, double* rhs,
-                                 double* factor, void* stream) {
+template <bool DW>
+static ph_status assemble(const ph_mesh* m, const double* a, double c, const double* f_face, const double* uD_face,
+                          const double* gN_face, double* values, double* rhs, double* factor, void* stream) {
   if (!m || !finite_pos(c)) return PH_ERR_ARG;
   if (m->nE > 0 && (!a || !f_face)) return PH_ERR_ARG;
   if ((m->nnz > 0 && !values) || (m->L > 0 && !rhs)) return PH_ERR_ARG;
@@ -168,12 +125,12 @@ extern "C" ph_status ph_assemble(const ph_mesh* m, const double* a, double c, co
   if (m->nE == 0) return PH_OK;
   const double c20 = c / 20.0, six_over_c = 6.0 / c;
   const unsigned grid = grid_for(m->nE, 128);
-#define PH_ASM(UDV, GNV, FACV)                                                                                 \
-  k_assemble<UDV, GNV, FACV><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->tpos, m->trel,        \
-                                                  m->face_area, a, c20, six_over_c, f_face, uD_face, gN_face, \
-                                                  values, rhs, factor, m->status)
+#define PH_ASM(UDV, GNV, FACV)                                                                                   \
+  k_assemble<UDV, GNV, FACV, DW><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->tpos, m->trel,      \
+                                                      m->face_area, a, c20, six_over_c, f_face, uD_face, gN_face, \
+                                                      values, rhs, factor, m->status)
   const bool ud = uD_face != nullptr && m->nFd > 0, gn = gN_face != nullptr && m->nFn > 0;
-  KernelTimer kt("k_assemble", s);
+  KernelTimer kt(DW ? "k_assemble_dw" : "k_assemble", s);
   if (factor) {
     if (ud && gn) PH_ASM(true, true, true);
     else if (ud) PH_ASM(true, false, true);
@@ -189,6 +146,18 @@ extern "C" ph_status ph_assemble(const ph_mesh* m, const double* a, double c, co
   const cudaError_t e = launched();
   kt.stop();
   return cuda_status(e, "k_assemble");
+}
+
+extern "C" ph_status ph_assemble(const ph_mesh* m, const double* a, double c, const double* f_face,
+                                 const double* uD_face, const double* gN_face, double* values, double* rhs,
+                                 double* factor, void* stream) {
+  return assemble<false>(m, a, c, f_face, uD_face, gN_face, values, rhs, factor, stream);
+}
+
+extern "C" ph_status ph_assemble_dw(const ph_mesh* m, const double* a, double c, const double* f_face,
+                                    const double* uD_face, const double* gN_face, double* values, double* rhs,
+                                    double* factor, void* stream) {
+  return assemble<true>(m, a, c, f_face, uD_face, gN_face, values, rhs, factor, stream);
 }
 
 extern "C" ph_status ph_recover(const ph_mesh* m, const double* a, double c, const double* f_face,

@@ -43,6 +43,8 @@ struct ProbDesc {
   double c20, six_over_c;
   int flags;  // bit 0: u_D, bit 1: g_N, bit 2: factor
   int pad;
+  const double* lambda;  // recovery (ph_batch_bind_recovery): face values in,
+  double* u;             // element values out
 };
 
 struct Tile {
@@ -72,6 +74,24 @@ __global__ void k_batch_assemble(const ProbDesc* __restrict__ probs, const Tile*
       case 5: run_tile<true, false, true>(d, tl.start, tl.count); break;
       case 6: run_tile<false, true, true>(d, tl.start, tl.count); break;
       default: run_tile<true, true, true>(d, tl.start, tl.count); break;
+    }
+  }
+}
+
+// persistent recovery from the element factor: the same tiles, each problem's
+// elements through the plain path's per-element code (recover_element_factored)
+__global__ void k_batch_recover(const ProbDesc* __restrict__ probs, const Tile* __restrict__ tiles, int64_t ntiles) {
+  for (int64_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
+    const Tile tl = tiles[k];
+    const ProbDesc& d = probs[tl.prob];
+    if (!d.u) continue;
+    for (int i = threadIdx.x; i < tl.count; i += blockDim.x) {
+      if (d.flags & 2)
+        recover_element_factored<true>(tl.start + i, d.geo, d.tface, d.tmult, d.area, d.factor, d.six_over_c, d.f,
+                                       d.gN, d.lambda, d.u);
+      else
+        recover_element_factored<false>(tl.start + i, d.geo, d.tface, d.tmult, d.area, d.factor, d.six_over_c, d.f,
+                                        d.gN, d.lambda, d.u);
     }
   }
 }
@@ -106,7 +126,7 @@ struct ph_batch {
   Tile* d_tiles;
   int64_t ntiles;
   int32_t tile, threads, blocks_per_sm, sms;
-  bool bound;
+  bool bound, recover;
   cudaGraph_t graph;
   cudaGraphExec_t exec;
 };
@@ -155,6 +175,7 @@ extern "C" ph_status ph_batch_create(ph_mesh* const* meshes, int32_t n, void* st
   b->graph = nullptr;
   b->exec = nullptr;
   b->bound = false;
+  b->recover = false;
   b->tile = 1024;
   b->threads = 128;
   b->blocks_per_sm = 4;
@@ -206,8 +227,16 @@ extern "C" ph_status ph_batch_bind(ph_batch* b, const double* const* a, const do
     if (!(c[i] > 0.0) || !(c[i] < INFINITY)) return PH_ERR_ARG;
     if (m->nE > 0 && (!a[i] || !f_face[i])) return PH_ERR_ARG;
     if ((m->nnz > 0 && !values[i]) || (m->L > 0 && !rhs[i])) return PH_ERR_ARG;
+    if (b->recover && b->host[i].u && (!factor || !factor[i])) return PH_ERR_ARG;  // recovery reads the factor
+  }
+  for (int32_t i = 0; i < b->n; ++i) {
+    const ph_mesh* m = b->meshes[i];
     ProbDesc& d = b->host[i];
+    const double* keep_lambda = d.lambda;  // recovery arrays survive a rebind
+    double* keep_u = d.u;
     memset(&d, 0, sizeof d);
+    d.lambda = keep_lambda;
+    d.u = keep_u;
     d.geo = m->geo;
     d.tface = m->tface;
     d.tmult = m->tmult;
@@ -248,9 +277,16 @@ static cudaError_t launch_batch(ph_batch* b, cudaStream_t s) {
   if (b->ntiles > 0) {
     const unsigned grid = (unsigned)std::min<int64_t>(b->ntiles, (int64_t)b->sms * b->blocks_per_sm);
     k_batch_assemble<<<grid, b->threads, 0, s>>>(b->d_probs, b->d_tiles, b->ntiles);
+    cudaError_t e = launched();
+    if (e != cudaSuccess || !b->recover) return e;
+    k_batch_recover<<<grid, b->threads, 0, s>>>(b->d_probs, b->d_tiles, b->ntiles);
     return launched();
   }
   return cudaSuccess;
+}
+
+static int batch_launches(const ph_batch* b) {
+  return (b->nrows > 0 ? 1 : 0) + (b->ntiles > 0 ? (b->recover ? 2 : 1) : 0);
 }
 
 extern "C" ph_status ph_batch_assemble(ph_batch* b, void* stream) {
@@ -351,6 +387,29 @@ extern "C" ph_status ph_batch_graph_launch(ph_batch* b, void* stream) {
     }
   }
   e = cudaGraphLaunch(b->exec, s);
-  if (e == cudaSuccess) g_launches.fetch_add((b->nrows > 0 ? 1 : 0) + (b->ntiles > 0 ? 1 : 0), std::memory_order_relaxed);
+  if (e == cudaSuccess) g_launches.fetch_add(batch_launches(b), std::memory_order_relaxed);
   return cuda_status(e, "ph_batch_graph_launch");
+}
+
+extern "C" ph_status ph_batch_bind_recovery(ph_batch* b, const double* const* lambda, double* const* u,
+                                            void* stream) {
+  if (!b || !b->bound) return PH_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool on = lambda != nullptr;
+  for (int32_t i = 0; i < b->n && on; ++i) {
+    const ph_mesh* m = b->meshes[i];
+    if (m->nE > 0 && (!u || !u[i] || !b->host[i].factor || (m->L > 0 && !lambda[i]))) return PH_ERR_ARG;
+  }
+  for (int32_t i = 0; i < b->n; ++i) {
+    b->host[i].lambda = on ? lambda[i] : nullptr;
+    b->host[i].u = on ? u[i] : nullptr;
+  }
+  cudaError_t e = cudaSuccess;
+  if (b->n > 0)
+    e = cudaMemcpyAsync(b->d_probs, b->host.data(), sizeof(ProbDesc) * b->n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e, "ph_batch_bind_recovery");
+  if (on != b->recover) drop_graph(b);  // the graph gains or loses the recovery launch
+  b->recover = on;
+  return PH_OK;
 }

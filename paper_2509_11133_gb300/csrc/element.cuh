@@ -3,6 +3,7 @@
 // element (see assemble.cu for the derivation).
 #pragma once
 
+#include "dw.cuh"
 #include "ph_internal.cuh"
 
 namespace ph_elem {
@@ -65,12 +66,92 @@ __device__ __forceinline__ void face_kernel(const Geo& G, double a, double c20, 
   Q[ut(3, 3)] = c0 + c1 + c2;
 }
 
+// The same Qf (times sc = sc6/6) with the 3x3 algebra in double-word
+// arithmetic on the FP32 pipe (dw.cuh), for the assembly variant of
+// ph_assemble_dw.  The element is first made dimensionless with exact powers
+// of two: G_e and G_e T0^-1 are scaled by 2^-k, 2^k the largest diagonal
+// entry's binade, so that
+//     Qv = 6 / (a |det E|) 2^k D0' (T0 + gamma G')^-1 G'T D0,
+//     G' = 2^-k G_e, G'T = 2^-k G_e T0^-1, gamma = c 2^k / (20 a),
+// and the double-word values stay within a few binades of 1; the scalar's
+// power of two goes into the conversion back to fp64.  The path is taken when
+// gamma G' is small against T0 (gamma 2^-k max g_ii <= 2^-2: the 3x3 matrix
+// then has condition number <= 6 and the double-word result is accurate to
+// ~1e-14 relative) and the element is not flat (|det E|^2 >= 2^-12 g00 g11
+// g22, judged on the exponents: the Kuhn elements and their refinements
+// sit near 2^-3, the jittered ones above 2^-10; on flatter elements the
+// condensation kernel's cancellations would cost the float pairs' 5 bits
+// fewer than fp64 more than the 1e-12 the results are held to).  Otherwise
+// -- a reaction term that dominates the element (c h^2 > a), a flat element,
+// or inputs beyond the exponent range -- it returns false and the caller
+// takes the fp64 path.
+__device__ __forceinline__ bool face_kernel_dw(const Geo& G, double a, double c20, double sc6, double Q[10]) {
+  using namespace dw;
+  const int e0 = exponent(G.g00), e1 = exponent(G.g11), e2 = exponent(G.g22);
+  const int kg = max(e0, max(e1, e2));
+  const int ka = exponent(a), kc = exponent(c20), kr = exponent(G.rdet);
+  const int p = kc + kg - ka;  // binade of gamma (within a factor 4)
+  const int K = kr - ka + kg;  // binade of the overall scalar 6/(a |det E|) 2^k (with sc)
+  const int flat = -2 * kr - (e0 + e1 + e2);  // binade of |det E|^2 / (g00 g11 g22), within a factor 16
+  if (p > -4 || flat < -12 || kg < -900 || kg > 900 || ka < -900 || ka > 900 || K < -900 || K > 900) return false;
+  const f2 am = from_double(a, -ka), cm = from_double(c20, -kc);  // mantissas in [1, 2)
+  const f2 ra = rcp(am);
+  const int s = -kg;
+  // gamma G' and the 3x3 matrix T0 + gamma G' (T0 = I + 1 1')
+  f2 m00, m01, m02, m11, m12, m22;
+  if (p < -100) {  // gamma G' below 2^-98 of T0: T0 alone
+    m00 = m11 = m22 = f2{2.f, 0.f};
+    m01 = m02 = m12 = f2{1.f, 0.f};
+  } else {
+    const f2 gam = ldexp(mul(cm, ra), p);
+    m00 = add(mul(gam, from_double(G.g00, s)), 2.f);
+    m11 = add(mul(gam, from_double(G.g11, s)), 2.f);
+    m22 = add(mul(gam, from_double(G.g22, s)), 2.f);
+    m01 = add(mul(gam, from_double(G.g01, s)), 1.f);
+    m02 = add(mul(gam, from_double(G.g02, s)), 1.f);
+    m12 = add(mul(gam, from_double(G.g12, s)), 1.f);
+  }
+  // adjugate and determinant
+  const f2 A00 = sub(mul(m11, m22), mul(m12, m12));
+  const f2 A01 = sub(mul(m02, m12), mul(m01, m22));
+  const f2 A02 = sub(mul(m01, m12), mul(m02, m11));
+  const f2 A11 = sub(mul(m00, m22), mul(m02, m02));
+  const f2 A12 = sub(mul(m01, m02), mul(m00, m12));
+  const f2 A22 = sub(mul(m00, m11), mul(m01, m01));
+  const f2 det = add(add(mul(m00, A00), mul(m01, A01)), mul(m02, A02));
+  // scalar: sc 6/(a |det E|) / det M' with its power of two 2^K kept apart
+  const f2 sc = mul(mul(mul(from_double(sc6), from_double(G.rdet, -kr)), ra), rcp(det));
+  const f2 t00 = from_double(G.t00, s), t01 = from_double(G.t01, s), t02 = from_double(G.t02, s);
+  const f2 t10 = from_double(G.t10, s), t11 = from_double(G.t11, s), t12 = from_double(G.t12, s);
+  const f2 t20 = from_double(G.t20, s), t21 = from_double(G.t21, s), t22 = from_double(G.t22, s);
+  // Y = adj(M') G'T (symmetric), scaled
+  const f2 y00 = mul(add(add(mul(A00, t00), mul(A01, t10)), mul(A02, t20)), sc);
+  const f2 y01 = mul(add(add(mul(A00, t01), mul(A01, t11)), mul(A02, t21)), sc);
+  const f2 y02 = mul(add(add(mul(A00, t02), mul(A01, t12)), mul(A02, t22)), sc);
+  const f2 y11 = mul(add(add(mul(A01, t01), mul(A11, t11)), mul(A12, t21)), sc);
+  const f2 y12 = mul(add(add(mul(A01, t02), mul(A11, t12)), mul(A12, t22)), sc);
+  const f2 y22 = mul(add(add(mul(A02, t02), mul(A12, t12)), mul(A22, t22)), sc);
+  // Qv = D0' Y D0; faces 0,1,2,3 sit opposite vertices 3,1,2,0
+  const f2 c0 = add(add(y00, y01), y02), c1 = add(add(y01, y11), y12), c2 = add(add(y02, y12), y22);
+  Q[ut(0, 0)] = to_double(y22, K);
+  Q[ut(0, 1)] = to_double(y02, K);
+  Q[ut(0, 2)] = to_double(y12, K);
+  Q[ut(0, 3)] = to_double(neg(c2), K);
+  Q[ut(1, 1)] = to_double(y00, K);
+  Q[ut(1, 2)] = to_double(y01, K);
+  Q[ut(1, 3)] = to_double(neg(c0), K);
+  Q[ut(2, 2)] = to_double(y11, K);
+  Q[ut(2, 3)] = to_double(neg(c1), K);
+  Q[ut(3, 3)] = to_double(add(add(c0, c1), c2), K);
+  return true;
+}
+
 using ph::neg_if;
 
 
 // Local matrices, condensation and scatter of element t (Section 4.2-4.3,
 // Eq. schur): the body of the assembly kernels (one thread per element).
-template <bool UD, bool GN, bool FAC>
+template <bool UD, bool GN, bool FAC, bool DW = false>
 __device__ __forceinline__ void assemble_element(int64_t t, const double* __restrict__ geo,
                                                  const int4* __restrict__ tface, const int4* __restrict__ tmult,
                                                  const int4* __restrict__ tpos, const ushort4* __restrict__ trel,
@@ -103,7 +184,7 @@ __device__ __forceinline__ void assemble_element(int64_t t, const double* __rest
     if (GN && comp(tm, k) == PH_NO_MULT) h[k] = fma(ar[k], __ldg(gN + F[k]), h[k]);
   }
   double Q[10];
-  face_kernel(G, at, c20, 6.0 / 9.0, Q);
+  if (!DW || !face_kernel_dw(G, at, c20, 6.0 / 9.0, Q)) face_kernel(G, at, c20, 6.0 / 9.0, Q);
   if (FAC) {
     double2* fo = reinterpret_cast<double2*>(factor + 10 * t);
     fo[0] = make_double2(Q[0], Q[1]);
@@ -163,6 +244,65 @@ __device__ __forceinline__ void assemble_element(int64_t t, const double* __rest
       ++idx;
     }
   }
+}
+
+__device__ __forceinline__ void store_u(double* __restrict__ u, int64_t t, const double U[4]) {
+  // vertex j holds U of the face opposite it: j = 0,1,2,3 <- k = 3,1,2,0
+  double2* out = reinterpret_cast<double2*>(u + 4 * t);
+  out[0] = make_double2(U[3], U[1]);
+  out[1] = make_double2(U[2], U[0]);
+}
+
+// z'_k = |T|/4 f(Ct_k) + |F_k| g(Ct_k) [Neumann] + d_k Lambda_k
+template <bool GN>
+__device__ __forceinline__ void recovery_load(double q4, int4 tf, int4 tm, const double* __restrict__ face_area,
+                                              const double* __restrict__ f_face, const double* __restrict__ gN,
+                                              const double* __restrict__ lambda, double z[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int F = comp(tf, k) & PH_ID_MASK;
+    const int mk = comp(tm, k);
+    const double ar = __ldg(face_area + F);
+    double zk = q4 * __ldg(f_face + F);
+    if (mk == PH_NO_MULT) {
+      if (GN) zk = fma(ar, __ldg(gN + F), zk);
+    } else {
+      zk = fma(neg_if(ar, comp(tf, k) < 0), __ldg(lambda + (mk & PH_ID_MASK)), zk);
+    }
+    z[k] = zk;
+  }
+}
+
+// Recovery of element t from the element factor Qf/9 stored by the assembly
+// (Algorithm 1, second loop): U[o(k)] = z'sum/(c|T|) - 3 (Qf/9 z')_k.  The
+// body of the plain and the batched recovery kernels.
+template <bool GN>
+__device__ __forceinline__ void recover_element_factored(int64_t t, const double* __restrict__ geo,
+                                                         const int4* __restrict__ tface,
+                                                         const int4* __restrict__ tmult,
+                                                         const double* __restrict__ face_area,
+                                                         const double* __restrict__ factor, double six_over_c,
+                                                         const double* __restrict__ f_face,
+                                                         const double* __restrict__ gN,
+                                                         const double* __restrict__ lambda, double* __restrict__ u) {
+  const double2 dr = __ldg(reinterpret_cast<const double2*>(geo + PH_GEO_STRIDE * t) + 7);  // (t22, |det|)
+  const double rdet = __ldg(geo + PH_GEO_STRIDE * t + 16);
+  double z[4];
+  recovery_load<GN>(dr.y * (1.0 / 24.0), __ldg(tface + t), __ldg(tmult + t), face_area, f_face, gN, lambda, z);
+  const double2* fp = reinterpret_cast<const double2*>(factor + 10 * t);
+  const double2 q0 = __ldg(fp), q1 = __ldg(fp + 1), q2 = __ldg(fp + 2), q3 = __ldg(fp + 3), q4 = __ldg(fp + 4);
+  const double Q[10] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y, q3.x, q3.y, q4.x, q4.y};
+  const double icT = rdet * six_over_c;
+  const double zs = icT * ((z[0] + z[1]) + (z[2] + z[3]));
+  double U[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double e = 0.0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) e = fma(Q[ut(k, m)], z[m], e);
+    U[k] = fma(-3.0, e, zs);
+  }
+  store_u(u, t, U);
 }
 
 }  // namespace ph_elem

@@ -1,0 +1,192 @@
+"""The double-word assembly variant (ph_assemble_dw) against the oracle, at the
+tolerances of the fp64 path: H entrywise relative 1e-12, rhs within 1e-12 of
+the sum of its addends' magnitudes, connectivity untouched.  Also: the element
+factor and H agree with the fp64 path to ~1e-13 (both approximate the same
+exact values), recovery from the variant's factor matches the oracle, and
+elements outside the double-word range (a reaction term that dominates, tiny
+coefficients) take the fp64 fallback and still match.
+
+Cases: every mesh of the fp64 parity tests (Listing 1 with and without mixed
+boundary data, Kuhn cubes, shuffled and degree-sorted meshes, the lognormal
+and jittered checkerboard workloads at small size), a soup of random
+isolated elements of graded flatness (slivers included) with diffusion- and
+reaction-dominated coefficients, and sampled rows of the full-size lognormal
+workload."""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+from tests.test_gpu_parity import CASES, assert_values_close, cu, host, make_case, run_oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ph():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2509_11133_gb300 as ph
+    from paper_2509_11133_gb300 import build
+    build.build()
+    ph.load()
+    return ph
+
+
+def run_both(ph, p, a=None, c=None):
+    """fp64 and double-word assembly of problem p on one mesh."""
+    a = p.a if a is None else a
+    c = p.c if c is None else c
+    mesh = ph.Mesh(cu(p.coord, torch.float64), cu(p.tet, torch.int32),
+                   cu(p.neumann, torch.int32) if p.neumann.size else None)
+    fc = {k: host(v) for k, v in mesh.faces().items()}
+    cen = fc["face_centroid"]
+    f = np.asarray(p.f(cen), np.float64)
+    uD = None if p.uD is None else np.asarray(p.uD(cen), np.float64)
+    gN = None if p.gN is None else np.asarray(p.gN(cen), np.float64)
+    opt = lambda x: None if x is None else cu(x, torch.float64)
+    out = {"mesh": mesh, "fc": fc, "f": f, "uD": uD, "gN": gN}
+    for variant in ("f64", "dw"):
+        v, r, fa = mesh.assemble(cu(a, torch.float64), c, cu(f, torch.float64), opt(uD), opt(gN), factor=True,
+                                 variant=variant)
+        out[variant] = {"values": host(v), "rhs": host(r), "factor": host(fa), "factor_d": fa}
+    mesh.check()
+    return out
+
+
+def assert_close_to_f64(g):
+    v64, vdw = g["f64"]["values"], g["dw"]["values"]
+    assert np.all(np.abs(vdw - v64) <= 1e-13 * np.abs(v64))
+    f64, fdw = g["f64"]["factor"], g["dw"]["factor"]
+    scale = np.abs(f64).max(axis=1, keepdims=True)
+    assert np.all(np.abs(fdw - f64) <= 1e-13 * scale)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_dw_assembly_parity(ph, name):
+    p = make_case(name)
+    g = run_both(ph, p)
+    o = run_oracle(p, f=g["f"], uD=g["uD"], gN=g["gN"])
+    assert_values_close({"values": g["dw"]["values"], "rhs": g["dw"]["rhs"]}, o)
+    assert_close_to_f64(g)
+    g["mesh"].close()
+
+
+@pytest.mark.parametrize("name", ["sin_kuhn", "mixed_l2", "lognormal_small", "jitter_checker_small"])
+def test_dw_factor_recovery_parity(ph, name):
+    p = make_case(name)
+    g = run_both(ph, p)
+    fc = oracle.faces(p.tet, p.nC, p.neumann)
+    fm, L = oracle.multipliers(fc["face_kind"])
+    lam = np.random.default_rng(2).standard_normal(L)
+    u = g["mesh"].recover_factored(g["dw"]["factor_d"], p.c, cu(g["f"], torch.float64), cu(lam, torch.float64),
+                                   None if g["gN"] is None else cu(g["gN"], torch.float64))
+    Uo = oracle.recover(p.coord, p.tet, fc, fm, p.a, p.c, g["f"], lam, g["gN"])
+    scale = np.abs(Uo).max(axis=1, keepdims=True)
+    assert np.all(np.abs(host(u) - Uo) <= 1e-12 * scale)
+    g["mesh"].close()
+
+
+def element_soup(n, seed, flat=(1e-3, 1.0)):
+    """n isolated elements (4 own vertices each, every face a boundary face):
+    regular tetrahedra, randomly rotated and jittered by 15% of their size,
+    whose vertex 3 is then pulled towards the plane of the other three,
+    leaving a height ratio log-uniform in `flat` (slivers at the low end:
+    |det E|^2 / (g00 g11 g22) ~ 0.5 ratio^2), sizes over three decades."""
+    rng = np.random.default_rng(seed)
+    base = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], float)
+    Qr, _ = np.linalg.qr(rng.standard_normal((n, 3, 3)))
+    P = np.einsum("vj,nij->nvi", base, Qr) + 0.15 * rng.standard_normal((n, 4, 3))
+    c3 = (P[:, 0] + P[:, 1] + P[:, 2]) / 3
+    nrm = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    off = np.einsum("ij,ij->i", P[:, 3] - c3, nrm)
+    keep = 10.0 ** rng.uniform(np.log10(flat[0]), np.log10(flat[1]), n)
+    P[:, 3] = P[:, 3] - (off * (1 - keep))[:, None] * nrm
+    P *= (10.0 ** rng.uniform(-2, 1, n))[:, None, None]
+    P += rng.uniform(-1, 1, (n, 1, 3))
+    coord = P.reshape(-1, 3)
+    tet = np.arange(4 * n, dtype=np.int32).reshape(n, 4)
+    return coord, tet
+
+
+def assert_soup_close(p, g, o, which):
+    """assert_values_close with a report of the worst element on failure
+    (in a soup, element t owns H entries 16t..16t+15)."""
+    v, w = g[which]["values"], o["values"]
+    err = np.abs(v - w) / np.abs(w)
+    if not np.all(err <= 1e-12):
+        t = int(np.argmax(err)) // 16
+        P = p.coord[p.tet[t]]
+        E = P[1:] - P[0]
+        det = abs(np.linalg.det(E))
+        ge = np.einsum("ij,ij->i", E, E)
+        print(f"{which}: worst error {err.max():.3e} at element {t}: a={p.a[t]:.3e} c={p.c} "
+              f"flatness det^2/prod(g)={det ** 2 / ge.prod():.3e} c h^2/a={p.c * ge.max() / p.a[t]:.3e}")
+    assert_values_close({"values": v, "rhs": g[which]["rhs"]}, o)
+
+
+@pytest.mark.parametrize("c", [1e-2, 1.0])
+def test_dw_element_soup_against_oracle(ph, c):
+    """Diffusion-dominated elements (a >= 1, sizes up to ~10, c <= 1) of any
+    shape, slivers included: both assemblies within 1e-12 of the oracle (the
+    flat ones take the fp64 path in the variant)."""
+    coord, tet = element_soup(4000, 11 + int(c * 100))
+    a = 10.0 ** np.random.default_rng(5).uniform(0, 4, tet.shape[0])
+    p = meshgen.Problem("soup", coord, tet, a, c, lambda x: meshgen.sin_source(x))
+    g = run_both(ph, p)
+    o = run_oracle(p, f=g["f"])
+    assert_soup_close(p, g, o, "f64")
+    assert_soup_close(p, g, o, "dw")
+    g["mesh"].close()
+
+
+def test_dw_fallback_elements(ph):
+    """A reaction term that dominates the element (c h^2 >> a) takes the fp64
+    path: every element of this soup (well shaped: the fp64 split form itself
+    needs G_e well conditioned when c h^2 >> a) does, so the result is the
+    fp64 path's bit for bit, and it matches the oracle."""
+    coord, tet = element_soup(2000, 3, flat=(0.3, 1.0))
+    a = 10.0 ** np.random.default_rng(9).uniform(-12, -6, tet.shape[0])
+    p = meshgen.Problem("fallback", coord, tet, a, 5.0, lambda x: meshgen.sin_source(x))
+    g = run_both(ph, p)
+    o = run_oracle(p, f=g["f"])
+    assert_soup_close(p, g, o, "dw")
+    for k in ("values", "rhs", "factor"):
+        assert np.array_equal(g["dw"][k].view(np.uint64), g["f64"][k].view(np.uint64)), k
+    g["mesh"].close()
+
+
+def test_dw_large_coefficients(ph):
+    """a in [1e8, 1e14] (the oracle's binary128 local solve stays accurate up
+    to a/(c h^2) ~ 1e20): the condensation kernel's scale 1/a travels as a
+    separate power of two; the double-word path matches the oracle."""
+    coord, tet = element_soup(1000, 4, flat=(1e-2, 1.0))  # the flattest take the fp64 path
+    a = 10.0 ** np.random.default_rng(10).uniform(8, 14, tet.shape[0])
+    p = meshgen.Problem("large", coord, tet, a, 0.5, lambda x: meshgen.sin_source(x))
+    g = run_both(ph, p)
+    o = run_oracle(p, f=g["f"])
+    assert_soup_close(p, g, o, "f64")
+    assert_soup_close(p, g, o, "dw")
+    assert_close_to_f64(g)
+    g["mesh"].close()
+
+
+def test_dw_full_size_sampled_rows(ph):
+    """The lognormal workload at full size (3,359,232 tets), the launch
+    configuration bench.py times: 2000 sampled rows of H and their rhs
+    entries against the oracle's element blocks."""
+    from tests.test_gpu_fullsize import check_sampled_rows
+    p = meshgen.problem("lognormal_3m")
+    dev = torch.device("cuda")
+    mesh = ph.Mesh(torch.as_tensor(p.coord, device=dev), torch.as_tensor(p.tet, device=dev))
+    fc = {k: v.cpu().numpy() for k, v in mesh.faces().items()}
+    f = np.asarray(p.f(fc["face_centroid"]), np.float64)
+    rowptr, colind = mesh.csr_pattern()
+    values, rhs = mesh.assemble(torch.as_tensor(p.a, device=dev), p.c, torch.as_tensor(f, device=dev), variant="dw")
+    mesh.check()
+    g = {"info": dict(mesh.info), "fc": fc, "f": f, "rowptr": rowptr.cpu().numpy(), "colind": colind.cpu().numpy(),
+         "values": values.cpu().numpy(), "rhs": rhs.cpu().numpy()}
+    mesh.close()
+    check_sampled_rows(p, g, np.random.default_rng(17))

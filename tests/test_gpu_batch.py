@@ -164,3 +164,39 @@ def test_config4_recipe_subset(ph):
     b.graph_launch()
     assert_identical(cases)
     b.close()
+
+
+def test_batched_recovery_in_the_graph(ph):
+    """Assembly and recovery of an uneven batch in one captured graph (three
+    launches): every problem's u bit-identical to ph_recover_factored on its
+    own factor, and the oracle's recovery within 1e-12."""
+    probs = problems()
+    cases = [Case(ph, p) for p in probs]
+    b = ph.Batch([c.mesh for c in cases])
+    b.bind([c.a for c in cases], [c.c for c in cases], [c.f for c in cases], [c.values for c in cases],
+           [c.rhs for c in cases], factor=[c.factor for c in cases], uD_face=[c.uD for c in cases],
+           gN_face=[c.gN for c in cases])
+    rng = np.random.default_rng(21)
+    lam = [cu(rng.standard_normal(c.mesh.L)) for c in cases]
+    us = [torch.full((c.mesh.nE, 4), np.nan, dtype=torch.float64, device="cuda") for c in cases]
+    b.bind_recovery(lam, us)
+    n0 = ph.ph_launch_count()
+    b.graph_launch()
+    torch.cuda.synchronize()
+    assert ph.ph_launch_count() - n0 == 3
+    for p, c, l, u in zip(probs, cases, lam, us):
+        v, r, fa = c.ref
+        ref = c.mesh.recover_factored(fa, c.c, c.f, l, c.gN)
+        assert torch.equal(u, ref), p.name
+        fc = oracle.faces(p.tet, p.nC, p.neumann if p.neumann.size else None)
+        fm, _ = oracle.multipliers(fc["face_kind"])
+        Uo = oracle.recover(p.coord, p.tet, fc, fm, p.a, c.c, c.f.cpu().numpy(), l.cpu().numpy(),
+                            None if c.gN is None else c.gN.cpu().numpy())
+        scale = np.abs(Uo).max(axis=1, keepdims=True)
+        assert np.all(np.abs(u.cpu().numpy() - Uo) <= 1e-12 * scale), p.name
+    b.bind_recovery(None, None)  # back to two launches
+    n0 = ph.ph_launch_count()
+    b.graph_launch()
+    torch.cuda.synchronize()
+    assert ph.ph_launch_count() - n0 == 2
+    b.close()
