@@ -304,15 +304,20 @@ def gpu_arm(args, rank, world, local_rank):
     for name in BUILD_KERNELS:
         ms, n = ph.ph_kernel_time(name, reset=True)
         build_kern[name] = ms / 5 if n else float("nan")  # per build (k_scan: all scans of one build)
-    # the precision variant: the same step with the condensation kernel in
-    # double-word arithmetic (ph_assemble_dw), its own timed loop
+    # the precision variant: the same step with the element geometry, the face
+    # areas and the condensation kernel in double-word arithmetic
+    # (ph_mesh_create_dw + ph_assemble_dw), its own timed loop
     variant = None
     if not args.no_variant:
         def step_dw(ev=None):
             if ev is not None:
                 ev[0].record(stream)
-            m = ph.Mesh(coord_d, tet_d)
+            m = ph.Mesh(coord_d, tet_d, geometry="dw")
+            if ev is not None:
+                ev[2].record(stream)
             m.assemble(a_d, p.c, f_d, values=values, rhs=rhs, factor=factor, variant="dw")
+            if ev is not None:
+                ev[3].record(stream)
             m.recover_factored(factor, p.c, f_d, lam_d, u=u)
             if ev is not None:
                 ev[1].record(stream)
@@ -322,7 +327,7 @@ def gpu_arm(args, rank, world, local_rank):
             step_dw()
             flush.zero_()
         torch.cuda.synchronize()
-        evd = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+        evd = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
         ph.ph_kernel_time("k_assemble_dw", reset=True)
         ph.ph_timing_enable(True)
         for i in range(args.steps):
@@ -331,7 +336,24 @@ def gpu_arm(args, rank, world, local_rank):
         torch.cuda.synchronize()
         ph.ph_timing_enable(False)
         ms, n = ph.ph_kernel_time("k_assemble_dw", reset=True)
+        # the double-word mesh build's kernels, in a short loop of their own
+        for name in BUILD_KERNELS:
+            ph.ph_kernel_time(name, reset=True)
+        ph.ph_timing_enable(2)
+        for _ in range(5):
+            step_dw()
+            flush.zero_()
+        torch.cuda.synchronize()
+        ph.ph_timing_enable(False)
+        build_dw = {}
+        for name in BUILD_KERNELS:
+            bms, bn = ph.ph_kernel_time(name, reset=True)
+            build_dw[name] = bms / 5 if bn else float("nan")
         variant = {"step_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in evd])),
+                   "mesh_build_kernels_ms": build_dw,
+                   "phases_ms": {"mesh_create_dw": float(np.mean([e[0].elapsed_time(e[2]) for e in evd])),
+                                 "assemble_dw": float(np.mean([e[2].elapsed_time(e[3]) for e in evd])),
+                                 "recover": float(np.mean([e[3].elapsed_time(e[1]) for e in evd]))},
                    "k_assemble_dw_ms": ms / n if n else float("nan")}
     # the FP64 pipe's throughput on this GPU, measured now, under the same
     # clock sampling as the timed steps: best of 3 probe launches
@@ -491,11 +513,14 @@ def variant_report(v, nE, nC, nF, world, fp64_peak_gops, hbm_peak, f64_step_ms, 
     prof = profile_figures("k_assemble_dw")
     bpt = assemble_bytes_per_tet(nE, nC, nF)
     out = {
-        "what": "ph_assemble_dw: the condensation kernel (the 3x3 algebra of A^-1) in double-word arithmetic "
-                "(float pairs, ~48 bits) on the FP32 pipe; leading terms, |det|, |F| and every sum of H and rhs "
-                "in fp64; same outputs as ph_assemble within 1e-13 (tested against the oracle at 1e-12)",
-        "dtype": "f64 + f32x2 (double-word) condensation kernel",
+        "what": "ph_mesh_create_dw + ph_assemble_dw + ph_recover_factored: the element geometry (G_e, G_e T0^-1), "
+                "the face areas and the condensation kernel (the 3x3 algebra of A^-1) in double-word arithmetic "
+                "(float pairs, ~48 bits) on the FP32 pipe; edge vectors, |det E|, the leading term d d'/(c|T|) "
+                "and every sum of H and rhs in fp64; flat or reaction-dominated elements take the fp64 kernel; "
+                "tested against the oracle at the fp64 path's tolerances (1e-12)",
+        "dtype": "f64 + f32x2 (double-word) geometry and condensation kernel",
         "value": whole_job_rate(nE, world, v["step_ms"]), "unit": UNIT, "ms_per_step": v["step_ms"],
+        "phases_ms": v["phases_ms"], "mesh_build_kernels_ms": v["mesh_build_kernels_ms"],
         "speedup_step_vs_f64": f64_step_ms / v["step_ms"],
         "k_assemble_dw_ms": v["k_assemble_dw_ms"], "speedup_kernel_vs_f64": f64_k_asm_ms / v["k_assemble_dw_ms"],
         "roofline_hbm": {"achieved": bpt * nE / k_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -784,7 +809,8 @@ def profile_kernels(workload, reps, variant="f64"):
     ph.load()
     dev = torch.device("cuda", 0)
     p = make_problem(workload)
-    mesh = ph.Mesh(torch.as_tensor(p.coord, device=dev), torch.as_tensor(p.tet, device=dev))
+    mesh = ph.Mesh(torch.as_tensor(p.coord, device=dev), torch.as_tensor(p.tet, device=dev),
+                   geometry="dw" if variant == "dw" else "f64")
     cen = mesh.faces()["face_centroid"].cpu().numpy()
     f = torch.as_tensor(np.asarray(p.f(cen), np.float64), device=dev)
     a = torch.as_tensor(p.a, device=dev)
@@ -797,7 +823,8 @@ def profile_kernels(workload, reps, variant="f64"):
         u = mesh.recover_factored(factor, p.c, f, lam)
         mesh.misfit(u, u_obs)
         mesh.adjoint_rhs(factor, p.c, u, u_obs)
-        mesh.adjoint_grad(a, factor, p.c, u, u_obs, q)
+        if variant == "f64":  # the gradient reads the fp64 geometry record
+            mesh.adjoint_grad(a, factor, p.c, u, u_obs, q)
     torch.cuda.synchronize()
     mesh.check()
     print(json.dumps({"profile_kernels": {"workload": workload, "nE": mesh.nE, "reps": reps, "variant": variant}}))

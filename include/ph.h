@@ -125,6 +125,21 @@ ph_status ph_mesh_create_batch(int32_t n, const double* const* coord, const int6
                                const int64_t* nE, const int32_t* const* neumann, const int64_t* nN, void* stream,
                                ph_mesh** out);
 
+/*
+ * ph_mesh_create for the double-word path (a precision variant; the paper has
+ * no counterpart): the same connectivity, numbering and CSR pattern, bit for
+ * bit, but the per-element geometry record holds G_e and G_e T0^-1 as scaled
+ * pairs of floats, computed in double-word arithmetic on the FP32 pipe from
+ * the fp64 edge vectors (|det E|, 1/|det E| and the face areas |F| stay the
+ * fp64 values: the leading terms of H and of the recovery need their last
+ * bits).  Such a mesh works with ph_assemble_dw, ph_recover_factored, ph_misfit,
+ * ph_adjoint_rhs and every connectivity, CSR and solver entry point; the
+ * entry points that read the fp64 record (ph_assemble, ph_recover,
+ * ph_adjoint_grad, ph_batch_create) return PH_ERR_ARG for it.
+ */
+ph_status ph_mesh_create_dw(const double* coord, int64_t nC, const int32_t* tet, int64_t nE,
+                            const int32_t* neumann, int64_t nN, void* stream, ph_mesh** out);
+
 /* Free a mesh.  Its device memory is released in `stream` order. */
 ph_status ph_mesh_destroy(ph_mesh* mesh, void* stream);
 

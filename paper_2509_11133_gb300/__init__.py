@@ -36,7 +36,7 @@ EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces",
            "ph_kernel_time", "ph_assemble_host", "ph_schwarz_create", "ph_schwarz_destroy",
            "ph_solve_pcg_schwarz", "ph_fp64_peak", "ph_test_fail_alloc", "ph_test_scan_withhold",
            "ph_pool_in_use", "ph_solve_refined", "ph_mesh_create_batch", "ph_host_mesh_query",
-           "ph_assemble_dw", "ph_batch_bind_recovery")
+           "ph_assemble_dw", "ph_batch_bind_recovery", "ph_mesh_create_dw")
 
 
 class PHError(RuntimeError):
@@ -69,6 +69,7 @@ def load(path: str | None = None):
     sig = {
         "ph_mesh_create": [P, I64, P, I64, P, I64, P, ctypes.POINTER(P)],
         "ph_mesh_create_batch": [I32, P, P, P, P, P, P, P, P],
+        "ph_mesh_create_dw": [P, I64, P, I64, P, I64, P, ctypes.POINTER(P)],
         "ph_host_mesh_query": [P, I64, P, I64, P, I64, ctypes.POINTER(ph_info), P, I64, P],
         "ph_mesh_destroy": [P, P],
         "ph_mesh_info": [P, ctypes.POINTER(ph_info)],
@@ -262,11 +263,13 @@ class Mesh:
     """A device mesh (``ph_mesh``): connectivity, CSR pattern and geometry.
 
     ``coord`` (nC x 3 float64) and ``tet`` (nE x 4 int32) are CUDA tensors;
-    ``neumann`` (nN x 3 int32) optional.  Methods allocate outputs with torch
-    and call the matching ``ph_*`` entry point on the current stream.
+    ``neumann`` (nN x 3 int32) optional.  geometry "dw" builds with
+    ph_mesh_create_dw (double-word geometry record, for ph_assemble_dw).
+    Methods allocate outputs with torch and call the matching ``ph_*`` entry
+    point on the current stream.
     """
 
-    def __init__(self, coord, tet, neumann=None, stream=None):
+    def __init__(self, coord, tet, neumann=None, stream=None, geometry="f64"):
         L = load()
         coord = coord.contiguous()
         tet = tet.contiguous()
@@ -275,11 +278,13 @@ class Mesh:
         nb = None if neumann is None or neumann.numel() == 0 else neumann.contiguous()
         if nb is not None and nb.dtype != torch.int32:
             raise ValueError("neumann int32")
+        if geometry not in ("f64", "dw"):
+            raise ValueError("geometry: 'f64' or 'dw'")
         h = ctypes.c_void_p()
         self._h = None
-        _check(L.ph_mesh_create(_ptr(coord), coord.shape[0], _ptr(tet), tet.shape[0], _ptr(nb),
-                                0 if nb is None else nb.shape[0], _stream(stream), ctypes.byref(h)),
-               "ph_mesh_create")
+        fn = L.ph_mesh_create if geometry == "f64" else L.ph_mesh_create_dw
+        _check(fn(_ptr(coord), coord.shape[0], _ptr(tet), tet.shape[0], _ptr(nb), 0 if nb is None else nb.shape[0],
+                  _stream(stream), ctypes.byref(h)), "ph_mesh_create" if geometry == "f64" else "ph_mesh_create_dw")
         self._adopt(h, coord.device)
 
     @classmethod

@@ -237,6 +237,10 @@ extern "C" ph_status ph_adjoint_grad(const ph_mesh* m, const double* a, const do
                                      const double* u, const double* u_obs, const double* q, double* grad,
                                      void* stream) {
   if (!m || !finite_pos(c)) return PH_ERR_ARG;
+  if (m->geo_dw) {  // the gradient reads G_e from the fp64 geometry record
+    set_error_text("ph_adjoint_grad: the mesh holds a double-word geometry record (ph_mesh_create_dw)");
+    return PH_ERR_ARG;
+  }
   if (m->nE > 0 && (!a || !factor || !u || !u_obs || !grad || (m->L > 0 && !q))) return PH_ERR_ARG;
   if (m->nE == 0) return PH_OK;
   cudaStream_t s = (cudaStream_t)stream;

@@ -28,6 +28,7 @@
 // "element factor", 10 numbers) so that ph_recover_factored skips the
 // condensation kernel.
 #include <math.h>
+#include <stdio.h>
 
 #include "element.cuh"
 #include "ph_internal.cuh"
@@ -36,19 +37,20 @@ using namespace ph_elem;
 
 namespace {
 
-template <bool UD, bool GN, bool FAC, bool DW>
-__global__ void __launch_bounds__(128) k_assemble(int64_t nE, const double* __restrict__ geo,
+template <bool UD, bool GN, bool FAC, int MODE>
+__global__ void __launch_bounds__(128, MODE ? 7 : 1) k_assemble(int64_t nE, const double* __restrict__ geo,
                                                   const int4* __restrict__ tface, const int4* __restrict__ tmult,
                                                   const int4* __restrict__ tpos, const ushort4* __restrict__ trel,
                                                   const double* __restrict__ face_area, const double* __restrict__ a,
                                                   double c20, double six_over_c, const double* __restrict__ f_face,
                                                   const double* __restrict__ uD, const double* __restrict__ gN,
                                                   double* __restrict__ values, double* __restrict__ rhs,
-                                                  double* __restrict__ factor, unsigned* status) {
+                                                  double* __restrict__ factor, unsigned* status,
+                                                  const double* __restrict__ coord, const int4* __restrict__ tet) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nE) return;
-  assemble_element<UD, GN, FAC, DW>(t, geo, tface, tmult, tpos, trel, face_area, a, c20, six_over_c, f_face, uD,
-                                    gN, values, rhs, factor, status);
+  assemble_element<UD, GN, FAC, MODE>(t, geo, tface, tmult, tpos, trel, face_area, a, c20, six_over_c, f_face, uD,
+                                      gN, values, rhs, factor, status, coord, tet);
 }
 
 
@@ -104,10 +106,43 @@ bool finite_pos(double x) { return x > 0.0 && x < INFINITY; }
 
 using namespace ph;
 
+// The fp64 entry points need the fp64 geometry record, which a mesh from
+// ph_mesh_create_dw does not hold.
+static bool needs_fp64_record(const ph_mesh* m, const char* who) {
+  if (!m->geo_dw) return false;
+  char msg[160];
+  snprintf(msg, sizeof msg, "%s: the mesh holds a double-word geometry record (ph_mesh_create_dw)", who);
+  set_error_text(msg);
+  return true;
+}
+
+template <int MODE>
+static void launch_assemble(const ph_mesh* m, unsigned grid, bool ud, bool gn, double c20, double six_over_c,
+                            const double* a, const double* f_face, const double* uD_face, const double* gN_face,
+                            double* values, double* rhs, double* factor, cudaStream_t s) {
+#define PH_ASM(UDV, GNV, FACV)                                                                                  \
+  k_assemble<UDV, GNV, FACV, MODE><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->tpos, m->trel,   \
+                                                        m->face_area, a, c20, six_over_c, f_face, uD_face,     \
+                                                        gN_face, values, rhs, factor, m->status, m->coord, m->tet)
+  if (factor) {
+    if (ud && gn) PH_ASM(true, true, true);
+    else if (ud) PH_ASM(true, false, true);
+    else if (gn) PH_ASM(false, true, true);
+    else PH_ASM(false, false, true);
+  } else {
+    if (ud && gn) PH_ASM(true, true, false);
+    else if (ud) PH_ASM(true, false, false);
+    else if (gn) PH_ASM(false, true, false);
+    else PH_ASM(false, false, false);
+  }
+#undef PH_ASM
+}
+
 template <bool DW>
 static ph_status assemble(const ph_mesh* m, const double* a, double c, const double* f_face, const double* uD_face,
                           const double* gN_face, double* values, double* rhs, double* factor, void* stream) {
   if (!m || !finite_pos(c)) return PH_ERR_ARG;
+  if (!DW && needs_fp64_record(m, "ph_assemble")) return PH_ERR_ARG;
   if (m->nE > 0 && (!a || !f_face)) return PH_ERR_ARG;
   if ((m->nnz > 0 && !values) || (m->L > 0 && !rhs)) return PH_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -125,24 +160,14 @@ static ph_status assemble(const ph_mesh* m, const double* a, double c, const dou
   if (m->nE == 0) return PH_OK;
   const double c20 = c / 20.0, six_over_c = 6.0 / c;
   const unsigned grid = grid_for(m->nE, 128);
-#define PH_ASM(UDV, GNV, FACV)                                                                                   \
-  k_assemble<UDV, GNV, FACV, DW><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->tpos, m->trel,      \
-                                                      m->face_area, a, c20, six_over_c, f_face, uD_face, gN_face, \
-                                                      values, rhs, factor, m->status)
   const bool ud = uD_face != nullptr && m->nFd > 0, gn = gN_face != nullptr && m->nFn > 0;
   KernelTimer kt(DW ? "k_assemble_dw" : "k_assemble", s);
-  if (factor) {
-    if (ud && gn) PH_ASM(true, true, true);
-    else if (ud) PH_ASM(true, false, true);
-    else if (gn) PH_ASM(false, true, true);
-    else PH_ASM(false, false, true);
-  } else {
-    if (ud && gn) PH_ASM(true, true, false);
-    else if (ud) PH_ASM(true, false, false);
-    else if (gn) PH_ASM(false, true, false);
-    else PH_ASM(false, false, false);
-  }
-#undef PH_ASM
+  if (!DW)
+    launch_assemble<0>(m, grid, ud, gn, c20, six_over_c, a, f_face, uD_face, gN_face, values, rhs, factor, s);
+  else if (!m->geo_dw)
+    launch_assemble<1>(m, grid, ud, gn, c20, six_over_c, a, f_face, uD_face, gN_face, values, rhs, factor, s);
+  else
+    launch_assemble<2>(m, grid, ud, gn, c20, six_over_c, a, f_face, uD_face, gN_face, values, rhs, factor, s);
   const cudaError_t e = launched();
   kt.stop();
   return cuda_status(e, "k_assemble");
@@ -163,6 +188,7 @@ extern "C" ph_status ph_assemble_dw(const ph_mesh* m, const double* a, double c,
 extern "C" ph_status ph_recover(const ph_mesh* m, const double* a, double c, const double* f_face,
                                 const double* gN_face, const double* lambda, double* u, void* stream) {
   if (!m || !finite_pos(c)) return PH_ERR_ARG;
+  if (needs_fp64_record(m, "ph_recover")) return PH_ERR_ARG;
   if (m->nE > 0 && (!a || !f_face || !u || (m->L > 0 && !lambda))) return PH_ERR_ARG;
   if (m->nE == 0) return PH_OK;
   cudaStream_t s = (cudaStream_t)stream;

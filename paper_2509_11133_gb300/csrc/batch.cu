@@ -162,8 +162,13 @@ static ph_status build_tiles(ph_batch* b, cudaStream_t s) {
 extern "C" ph_status ph_batch_create(ph_mesh* const* meshes, int32_t n, void* stream, ph_batch** out) {
   if (!out || n < 0 || (n > 0 && !meshes)) return PH_ERR_ARG;
   *out = nullptr;
-  for (int32_t i = 0; i < n; ++i)
+  for (int32_t i = 0; i < n; ++i) {
     if (!meshes[i]) return PH_ERR_ARG;
+    if (meshes[i]->geo_dw) {  // the batched kernel runs the fp64 element code
+      set_error_text("ph_batch_create: a mesh holds a double-word geometry record (ph_mesh_create_dw)");
+      return PH_ERR_ARG;
+    }
+  }
   cudaStream_t s = (cudaStream_t)stream;
   ph_batch* b = new ph_batch();
   b->n = n;

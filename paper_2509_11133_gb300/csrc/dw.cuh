@@ -84,6 +84,9 @@ __device__ __forceinline__ f2 rcp(f2 y) {
   return add(mul(e, t), t);
 }
 
+// Binade of a nonzero normal float (bit pattern).
+__device__ __forceinline__ int exponent(float x) { return (int)((__float_as_uint(x) >> 23) & 0xFF) - 127; }
+
 // x * 2^p for an integer p in [-126, 127] (exact while the result is normal)
 __device__ __forceinline__ f2 ldexp(f2 x, int p) {
   const float s = __uint_as_float((unsigned)(p + 127) << 23);

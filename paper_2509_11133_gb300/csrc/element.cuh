@@ -24,6 +24,43 @@ struct Geo {
   double adet, rdet;
 };
 
+// Element geometry of tet [P0 P1 P2 P3] in fp64: E = rows P_i - P_0
+// (i = 1..3), G_e = E E', GT = G_e T0^-1 = G_e - (G_e 1) 1'/4 (T0 = I + 1 1';
+// one fma per entry, the quarter being exact), |det E| and 1/|det E| (the
+// Newton reciprocal).  The mesh build stores it as the element's fp64
+// record; the double-word kernels recompute it for elements they hand to the
+// fp64 path.
+__device__ __forceinline__ Geo compute_geo(const double* __restrict__ coord, int4 v) {
+  const double* p0 = coord + 3 * (int64_t)v.x;
+  const double* p1 = coord + 3 * (int64_t)v.y;
+  const double* p2 = coord + 3 * (int64_t)v.z;
+  const double* p3 = coord + 3 * (int64_t)v.w;
+  const double e1x = p1[0] - p0[0], e1y = p1[1] - p0[1], e1z = p1[2] - p0[2];
+  const double e2x = p2[0] - p0[0], e2y = p2[1] - p0[1], e2z = p2[2] - p0[2];
+  const double e3x = p3[0] - p0[0], e3y = p3[1] - p0[1], e3z = p3[2] - p0[2];
+  const double det = e1x * (e2y * e3z - e2z * e3y) + e1y * (e2z * e3x - e2x * e3z) + e1z * (e2x * e3y - e2y * e3x);
+  Geo G;
+  G.adet = ph::neg_if(det, __double2hiint(det) < 0);  // |det| on the sign bit
+  G.g00 = e1x * e1x + e1y * e1y + e1z * e1z;
+  G.g01 = e1x * e2x + e1y * e2y + e1z * e2z;
+  G.g02 = e1x * e3x + e1y * e3y + e1z * e3z;
+  G.g11 = e2x * e2x + e2y * e2y + e2z * e2z;
+  G.g12 = e2x * e3x + e2y * e3y + e2z * e3z;
+  G.g22 = e3x * e3x + e3y * e3y + e3z * e3z;
+  const double r0 = (G.g00 + G.g01) + G.g02, r1 = (G.g01 + G.g11) + G.g12, r2 = (G.g02 + G.g12) + G.g22;
+  G.t00 = fma(-0.25, r0, G.g00);
+  G.t01 = fma(-0.25, r0, G.g01);
+  G.t02 = fma(-0.25, r0, G.g02);
+  G.t10 = fma(-0.25, r1, G.g01);
+  G.t11 = fma(-0.25, r1, G.g11);
+  G.t12 = fma(-0.25, r1, G.g12);
+  G.t20 = fma(-0.25, r2, G.g02);
+  G.t21 = fma(-0.25, r2, G.g12);
+  G.t22 = fma(-0.25, r2, G.g22);
+  G.rdet = ph::rcp_newton(G.adet);
+  return G;
+}
+
 __device__ __forceinline__ Geo load_geo(const double* __restrict__ geo, int64_t t) {
   const double2* p = reinterpret_cast<const double2*>(geo + PH_GEO_STRIDE * t);
   const double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3), e = __ldg(p + 4);
@@ -66,6 +103,72 @@ __device__ __forceinline__ void face_kernel(const Geo& G, double a, double c20, 
   Q[ut(3, 3)] = c0 + c1 + c2;
 }
 
+// The geometry of one element in double-word form: G' = 2^-kg G_e and
+// G'T = 2^-kg G_e T0^-1, 2^kg the binade of the largest diagonal entry of
+// G_e (so every value is below ~8 in magnitude), |det E| and 1/|det E| in
+// fp64, and the binade of |det E|^2 / (g00 g11 g22) (the element's
+// flatness, within a factor 16).
+struct GeoDW {
+  dw::f2 g[6];  // G' 00 01 02 11 12 22
+  dw::f2 t[9];  // G'T row-major
+  double adet, rdet;
+  int kg, flat;
+};
+
+// The double-word geometry from the fp64 record (integer conversions).
+__device__ __forceinline__ GeoDW geo_dw_from(const Geo& G) {
+  using namespace dw;
+  GeoDW D;
+  const int e0 = exponent(G.g00), e1 = exponent(G.g11), e2 = exponent(G.g22);
+  D.kg = max(e0, max(e1, e2));
+  D.flat = -2 * exponent(G.rdet) - (e0 + e1 + e2);
+  const int s = -D.kg;
+  D.g[0] = from_double(G.g00, s);
+  D.g[1] = from_double(G.g01, s);
+  D.g[2] = from_double(G.g02, s);
+  D.g[3] = from_double(G.g11, s);
+  D.g[4] = from_double(G.g12, s);
+  D.g[5] = from_double(G.g22, s);
+  D.t[0] = from_double(G.t00, s);
+  D.t[1] = from_double(G.t01, s);
+  D.t[2] = from_double(G.t02, s);
+  D.t[3] = from_double(G.t10, s);
+  D.t[4] = from_double(G.t11, s);
+  D.t[5] = from_double(G.t12, s);
+  D.t[6] = from_double(G.t20, s);
+  D.t[7] = from_double(G.t21, s);
+  D.t[8] = from_double(G.t22, s);
+  D.adet = G.adet;
+  D.rdet = G.rdet;
+  return D;
+}
+
+// The double-word record of a mesh built by ph_mesh_create_dw (same 144 bytes
+// per element as the fp64 record: 30 floats of pairs, then |det E| and
+// 1/|det E| as doubles 15 and 16, then kg and the flatness as two ints).
+__device__ __forceinline__ GeoDW load_geo_dw(const double* __restrict__ geo, int64_t t) {
+  const float4* p = reinterpret_cast<const float4*>(geo + PH_GEO_STRIDE * t);
+  float v[36];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float4 q = __ldg(p + i);
+    v[4 * i] = q.x;
+    v[4 * i + 1] = q.y;
+    v[4 * i + 2] = q.z;
+    v[4 * i + 3] = q.w;
+  }
+  GeoDW D;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) D.g[i] = dw::f2{v[2 * i], v[2 * i + 1]};
+#pragma unroll
+  for (int i = 0; i < 9; ++i) D.t[i] = dw::f2{v[12 + 2 * i], v[13 + 2 * i]};
+  D.adet = __hiloint2double(__float_as_int(v[31]), __float_as_int(v[30]));
+  D.rdet = __hiloint2double(__float_as_int(v[33]), __float_as_int(v[32]));
+  D.kg = __float_as_int(v[34]);
+  D.flat = __float_as_int(v[35]);
+  return D;
+}
+
 // The same Qf (times sc = sc6/6) with the 3x3 algebra in double-word
 // arithmetic on the FP32 pipe (dw.cuh), for the assembly variant of
 // ph_assemble_dw.  The element is first made dimensionless with exact powers
@@ -85,18 +188,15 @@ __device__ __forceinline__ void face_kernel(const Geo& G, double a, double c20, 
 // -- a reaction term that dominates the element (c h^2 > a), a flat element,
 // or inputs beyond the exponent range -- it returns false and the caller
 // takes the fp64 path.
-__device__ __forceinline__ bool face_kernel_dw(const Geo& G, double a, double c20, double sc6, double Q[10]) {
+__device__ __forceinline__ bool face_kernel_dw(const GeoDW& D, double a, double c20, double sc6, double Q[10]) {
   using namespace dw;
-  const int e0 = exponent(G.g00), e1 = exponent(G.g11), e2 = exponent(G.g22);
-  const int kg = max(e0, max(e1, e2));
-  const int ka = exponent(a), kc = exponent(c20), kr = exponent(G.rdet);
+  const int kg = D.kg;
+  const int ka = exponent(a), kc = exponent(c20), kr = exponent(D.rdet);
   const int p = kc + kg - ka;  // binade of gamma (within a factor 4)
   const int K = kr - ka + kg;  // binade of the overall scalar 6/(a |det E|) 2^k (with sc)
-  const int flat = -2 * kr - (e0 + e1 + e2);  // binade of |det E|^2 / (g00 g11 g22), within a factor 16
-  if (p > -4 || flat < -12 || kg < -900 || kg > 900 || ka < -900 || ka > 900 || K < -900 || K > 900) return false;
+  if (p > -4 || D.flat < -12 || kg < -900 || kg > 900 || ka < -900 || ka > 900 || K < -900 || K > 900) return false;
   const f2 am = from_double(a, -ka), cm = from_double(c20, -kc);  // mantissas in [1, 2)
   const f2 ra = rcp(am);
-  const int s = -kg;
   // gamma G' and the 3x3 matrix T0 + gamma G' (T0 = I + 1 1')
   f2 m00, m01, m02, m11, m12, m22;
   if (p < -100) {  // gamma G' below 2^-98 of T0: T0 alone
@@ -104,12 +204,12 @@ __device__ __forceinline__ bool face_kernel_dw(const Geo& G, double a, double c2
     m01 = m02 = m12 = f2{1.f, 0.f};
   } else {
     const f2 gam = ldexp(mul(cm, ra), p);
-    m00 = add(mul(gam, from_double(G.g00, s)), 2.f);
-    m11 = add(mul(gam, from_double(G.g11, s)), 2.f);
-    m22 = add(mul(gam, from_double(G.g22, s)), 2.f);
-    m01 = add(mul(gam, from_double(G.g01, s)), 1.f);
-    m02 = add(mul(gam, from_double(G.g02, s)), 1.f);
-    m12 = add(mul(gam, from_double(G.g12, s)), 1.f);
+    m00 = add(mul(gam, D.g[0]), 2.f);
+    m01 = add(mul(gam, D.g[1]), 1.f);
+    m02 = add(mul(gam, D.g[2]), 1.f);
+    m11 = add(mul(gam, D.g[3]), 2.f);
+    m12 = add(mul(gam, D.g[4]), 1.f);
+    m22 = add(mul(gam, D.g[5]), 2.f);
   }
   // adjugate and determinant
   const f2 A00 = sub(mul(m11, m22), mul(m12, m12));
@@ -120,17 +220,15 @@ __device__ __forceinline__ bool face_kernel_dw(const Geo& G, double a, double c2
   const f2 A22 = sub(mul(m00, m11), mul(m01, m01));
   const f2 det = add(add(mul(m00, A00), mul(m01, A01)), mul(m02, A02));
   // scalar: sc 6/(a |det E|) / det M' with its power of two 2^K kept apart
-  const f2 sc = mul(mul(mul(from_double(sc6), from_double(G.rdet, -kr)), ra), rcp(det));
-  const f2 t00 = from_double(G.t00, s), t01 = from_double(G.t01, s), t02 = from_double(G.t02, s);
-  const f2 t10 = from_double(G.t10, s), t11 = from_double(G.t11, s), t12 = from_double(G.t12, s);
-  const f2 t20 = from_double(G.t20, s), t21 = from_double(G.t21, s), t22 = from_double(G.t22, s);
+  const f2 sc = mul(mul(mul(from_double(sc6), from_double(D.rdet, -kr)), ra), rcp(det));
+  const f2* t = D.t;
   // Y = adj(M') G'T (symmetric), scaled
-  const f2 y00 = mul(add(add(mul(A00, t00), mul(A01, t10)), mul(A02, t20)), sc);
-  const f2 y01 = mul(add(add(mul(A00, t01), mul(A01, t11)), mul(A02, t21)), sc);
-  const f2 y02 = mul(add(add(mul(A00, t02), mul(A01, t12)), mul(A02, t22)), sc);
-  const f2 y11 = mul(add(add(mul(A01, t01), mul(A11, t11)), mul(A12, t21)), sc);
-  const f2 y12 = mul(add(add(mul(A01, t02), mul(A11, t12)), mul(A12, t22)), sc);
-  const f2 y22 = mul(add(add(mul(A02, t02), mul(A12, t12)), mul(A22, t22)), sc);
+  const f2 y00 = mul(add(add(mul(A00, t[0]), mul(A01, t[3])), mul(A02, t[6])), sc);
+  const f2 y01 = mul(add(add(mul(A00, t[1]), mul(A01, t[4])), mul(A02, t[7])), sc);
+  const f2 y02 = mul(add(add(mul(A00, t[2]), mul(A01, t[5])), mul(A02, t[8])), sc);
+  const f2 y11 = mul(add(add(mul(A01, t[1]), mul(A11, t[4])), mul(A12, t[7])), sc);
+  const f2 y12 = mul(add(add(mul(A01, t[2]), mul(A11, t[5])), mul(A12, t[8])), sc);
+  const f2 y22 = mul(add(add(mul(A02, t[2]), mul(A12, t[5])), mul(A22, t[8])), sc);
   // Qv = D0' Y D0; faces 0,1,2,3 sit opposite vertices 3,1,2,0
   const f2 c0 = add(add(y00, y01), y02), c1 = add(add(y01, y11), y12), c2 = add(add(y02, y12), y22);
   Q[ut(0, 0)] = to_double(y22, K);
@@ -151,7 +249,11 @@ using ph::neg_if;
 
 // Local matrices, condensation and scatter of element t (Section 4.2-4.3,
 // Eq. schur): the body of the assembly kernels (one thread per element).
-template <bool UD, bool GN, bool FAC, bool DW = false>
+// MODE: 0 fp64 (the fp64 record, face_kernel); 1 the double-word face
+// kernel on the fp64 record (converted); 2 the double-word record of a mesh
+// from ph_mesh_create_dw (elements the double-word kernel hands back get
+// their fp64 geometry recomputed from coord and tet).
+template <bool UD, bool GN, bool FAC, int MODE = 0>
 __device__ __forceinline__ void assemble_element(int64_t t, const double* __restrict__ geo,
                                                  const int4* __restrict__ tface, const int4* __restrict__ tmult,
                                                  const int4* __restrict__ tpos, const ushort4* __restrict__ trel,
@@ -159,13 +261,24 @@ __device__ __forceinline__ void assemble_element(int64_t t, const double* __rest
                                                  double c20, double six_over_c, const double* __restrict__ f_face,
                                                  const double* __restrict__ uD, const double* __restrict__ gN,
                                                  double* __restrict__ values, double* __restrict__ rhs,
-                                                 double* __restrict__ factor, unsigned* status) {
+                                                 double* __restrict__ factor, unsigned* status,
+                                                 const double* __restrict__ coord = nullptr,
+                                                 const int4* __restrict__ tet = nullptr) {
   const double at = __ldg(a + t);
   if (!ph::pos_finite(at)) {
     ph_flag(status, PH_ERR_ARG);
     return;
   }
-  const Geo G = load_geo(geo, t);
+  Geo G;
+  GeoDW D;
+  if (MODE == 2) {
+    D = load_geo_dw(geo, t);
+    G.adet = D.adet;
+    G.rdet = D.rdet;
+  } else {
+    G = load_geo(geo, t);
+    if (MODE == 1) D = geo_dw_from(G);
+  }
   const int4 tf = __ldg(tface + t);
   const int4 tm = __ldg(tmult + t);
   int F[4];
@@ -184,7 +297,12 @@ __device__ __forceinline__ void assemble_element(int64_t t, const double* __rest
     if (GN && comp(tm, k) == PH_NO_MULT) h[k] = fma(ar[k], __ldg(gN + F[k]), h[k]);
   }
   double Q[10];
-  if (!DW || !face_kernel_dw(G, at, c20, 6.0 / 9.0, Q)) face_kernel(G, at, c20, 6.0 / 9.0, Q);
+  if (MODE == 0) {
+    face_kernel(G, at, c20, 6.0 / 9.0, Q);
+  } else if (!face_kernel_dw(D, at, c20, 6.0 / 9.0, Q)) {
+    if (MODE == 2) G = compute_geo(coord, __ldg(tet + t));
+    face_kernel(G, at, c20, 6.0 / 9.0, Q);
+  }
   if (FAC) {
     double2* fo = reinterpret_cast<double2*>(factor + 10 * t);
     fo[0] = make_double2(Q[0], Q[1]);

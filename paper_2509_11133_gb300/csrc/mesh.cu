@@ -18,6 +18,7 @@
 #include <vector>
 
 
+#include "element.cuh"
 #include "ph_internal.cuh"
 
 namespace {
@@ -71,37 +72,100 @@ __device__ __forceinline__ int64_t bucket_of(int3 s, int sub) {
   return ((int64_t)s.z << sub) | ((s.x ^ s.y) & ((1 << sub) - 1));
 }
 
-// Element geometry of tet t = [P0 P1 P2 P3]: E = rows P_i - P_0 (i = 1..3),
-// G_e = E E', GT = G_e T0^-1 = G_e - (G_e 1) 1'/4 (T0 = I + 1 1'), |det E|,
-// 1/|det E|.
+// Element geometry record of tet t (fp64; compute_geo): G_e, G_e T0^-1,
+// |det E|, 1/|det E|.
 __device__ __forceinline__ void tet_geom(const double* __restrict__ coord, int4 v, int64_t t,
                                          double* __restrict__ geo, unsigned* status) {
+  const ph_elem::Geo G = ph_elem::compute_geo(coord, v);
+  if (!ph::pos_finite(G.adet)) ph_flag(status, PH_ERR_DEGENERATE);
+  double2* gg = reinterpret_cast<double2*>(geo + PH_GEO_STRIDE * t);
+  gg[0] = make_double2(G.g00, G.g01);
+  gg[1] = make_double2(G.g02, G.g11);
+  gg[2] = make_double2(G.g12, G.g22);
+  gg[3] = make_double2(G.t00, G.t01);
+  gg[4] = make_double2(G.t02, G.t10);
+  gg[5] = make_double2(G.t11, G.t12);
+  gg[6] = make_double2(G.t20, G.t21);
+  gg[7] = make_double2(G.t22, G.adet);
+  gg[8] = make_double2(G.rdet, 0.0);
+}
+
+// The double-word geometry record of tet t (meshes of ph_mesh_create_dw):
+// E, det E, |det E| and 1/|det E| in fp64 as in compute_geo (so |det E| and
+// 1/|det E| are the fp64 record's bits), then E scaled by the power of two
+// of its largest entry, G' = E'E'^T, its scale 2^kg and G'T = G' - (G' 1) 1'/4
+// in double-word (dw.cuh), stored as the layout of load_geo_dw reads it.
+__device__ __forceinline__ void tet_geom_dw(const double* __restrict__ coord, int4 v, int64_t t,
+                                            double* __restrict__ geo, unsigned* status) {
+  using namespace dw;
   const double* p0 = coord + 3 * (int64_t)v.x;
   const double* p1 = coord + 3 * (int64_t)v.y;
   const double* p2 = coord + 3 * (int64_t)v.z;
   const double* p3 = coord + 3 * (int64_t)v.w;
-  const double e1x = p1[0] - p0[0], e1y = p1[1] - p0[1], e1z = p1[2] - p0[2];
-  const double e2x = p2[0] - p0[0], e2y = p2[1] - p0[1], e2z = p2[2] - p0[2];
-  const double e3x = p3[0] - p0[0], e3y = p3[1] - p0[1], e3z = p3[2] - p0[2];
-  const double det = e1x * (e2y * e3z - e2z * e3y) + e1y * (e2z * e3x - e2x * e3z) + e1z * (e2x * e3y - e2y * e3x);
-  const double adet = ph::neg_if(det, __double2hiint(det) < 0);  // |det| on the sign bit
+  double e[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    e[0][d] = p1[d] - p0[d];
+    e[1][d] = p2[d] - p0[d];
+    e[2][d] = p3[d] - p0[d];
+  }
+  const double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) +
+                     e[0][1] * (e[1][2] * e[2][0] - e[1][0] * e[2][2]) +
+                     e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+  const double adet = ph::neg_if(det, __double2hiint(det) < 0);
   if (!ph::pos_finite(adet)) ph_flag(status, PH_ERR_DEGENERATE);
-  const double g00 = e1x * e1x + e1y * e1y + e1z * e1z, g01 = e1x * e2x + e1y * e2y + e1z * e2z;
-  const double g02 = e1x * e3x + e1y * e3y + e1z * e3z, g11 = e2x * e2x + e2y * e2y + e2z * e2z;
-  const double g12 = e2x * e3x + e2y * e3y + e2z * e3z, g22 = e3x * e3x + e3y * e3y + e3z * e3z;
-  // row sums of G_e; G_e T0^-1 = G_e - (row sum / 4) 1' as one fma per entry
-  // (the quarter is exact, so this rounds like the plain difference)
-  const double r0 = (g00 + g01) + g02, r1 = (g01 + g11) + g12, r2 = (g02 + g12) + g22;
-  double2* gg = reinterpret_cast<double2*>(geo + PH_GEO_STRIDE * t);
-  gg[0] = make_double2(g00, g01);
-  gg[1] = make_double2(g02, g11);
-  gg[2] = make_double2(g12, g22);
-  gg[3] = make_double2(fma(-0.25, r0, g00), fma(-0.25, r0, g01));
-  gg[4] = make_double2(fma(-0.25, r0, g02), fma(-0.25, r1, g01));
-  gg[5] = make_double2(fma(-0.25, r1, g11), fma(-0.25, r1, g12));
-  gg[6] = make_double2(fma(-0.25, r2, g02), fma(-0.25, r2, g12));
-  gg[7] = make_double2(fma(-0.25, r2, g22), adet);
-  gg[8] = make_double2(ph::rcp_newton(adet), 0.0);
+  const double rdet = ph::rcp_newton(adet);
+  int kE = -1023;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) kE = max(kE, exponent(e[i][d]));
+  f2 E[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) E[i][d] = from_double(e[i][d], -kE);
+  f2 g[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) g[i][j] = add(add(mul(E[i][0], E[j][0]), mul(E[i][1], E[j][1])), mul(E[i][2], E[j][2]));
+  const int kd = max(exponent(g[0][0].h), max(exponent(g[1][1].h), exponent(g[2][2].h)));
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) g[i][j] = ldexp(g[i][j], -kd);
+  g[1][0] = g[0][1];
+  g[2][0] = g[0][2];
+  g[2][1] = g[1][2];
+  float out[36];
+  const f2 gs[6] = {g[0][0], g[0][1], g[0][2], g[1][1], g[1][2], g[2][2]};
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    out[2 * i] = gs[i].h;
+    out[2 * i + 1] = gs[i].l;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const f2 q = ldexp(add(add(g[i][0], g[i][1]), g[i][2]), -2);  // row sum / 4 (exact scaling)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const f2 tij = sub(g[i][j], q);
+      out[12 + 2 * (3 * i + j)] = tij.h;
+      out[13 + 2 * (3 * i + j)] = tij.l;
+    }
+  }
+  const int kg = 2 * kE + kd;
+  out[30] = __int_as_float(__double2loint(adet));
+  out[31] = __int_as_float(__double2hiint(adet));
+  out[32] = __int_as_float(__double2loint(rdet));
+  out[33] = __int_as_float(__double2hiint(rdet));
+  out[34] = __int_as_float(kg);
+  out[35] = __int_as_float(-2 * exponent(rdet) - (exponent(g[0][0].h) + exponent(g[1][1].h) + exponent(g[2][2].h) +
+                                                  3 * kg));
+  float4* o = reinterpret_cast<float4*>(geo + PH_GEO_STRIDE * t);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) o[i] = make_float4(out[4 * i], out[4 * i + 1], out[4 * i + 2], out[4 * i + 3]);
 }
 
 // 1. histogram of face keys by bucket
@@ -130,7 +194,7 @@ __global__ void k_face_count(const int4* __restrict__ tet, int64_t nE, int64_t n
 __global__ void k_face_fill(const int4* __restrict__ tet, int64_t nE, int64_t nC, const int32_t* __restrict__ nb,
                             int64_t nN, int sub, const int32_t* __restrict__ start, int32_t* __restrict__ cnt,
                             int4* __restrict__ entries, int32_t* __restrict__ mate, const double* __restrict__ coord,
-                            double* __restrict__ geo, unsigned* status) {
+                            double* __restrict__ geo, bool geo_dw, unsigned* status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (failed(status)) return;
   if (i < nE) {
@@ -144,7 +208,8 @@ __global__ void k_face_fill(const int4* __restrict__ tet, int64_t nE, int64_t nC
       entries[pos] = make_int4(s.x, s.y, s.z, (int)(4 * i + k));
     }
     reinterpret_cast<int4*>(mate)[i] = make_int4(-1, -1, -1, -1);  // no mate yet (boundary)
-    tet_geom(coord, v, i, geo, status);
+    if (geo_dw) tet_geom_dw(coord, v, i, geo, status);
+    else tet_geom(coord, v, i, geo, status);
   } else if (i < nE + nN) {
     int3 f = neumann_tri(nb, i - nE);
     if (!valid_tri(f, nC)) return;
@@ -493,36 +558,42 @@ static void mesh_free(ph_mesh* m, cudaStream_t s) {
   delete m;
 }
 
-// Per-problem counts of a batched build (the union mesh of ph_mesh_create_batch):
-// problem p owns tets [toff[p], toff[p+1]); a face belongs to the problem of
-// its T+ tet.  counts[3p..3p+2] += faces, multipliers, CSR entries of rows.
-__global__ void k_batch_counts(const int2* __restrict__ face_tet, const int32_t* __restrict__ face_mult,
-                               const int32_t* __restrict__ rowptr, const int64_t* __restrict__ d_tot, int64_t nFmax,
-                               const int64_t* __restrict__ toff, int32_t n, unsigned long long* __restrict__ counts,
-                               const unsigned* status) {
-  const int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (F >= nFmax || F >= d_tot[0] || failed(status)) return;
-  const int64_t t = face_tet[F].x;
-  int lo = 0, hi = n - 1;  // last p with toff[p] <= t
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (toff[mid] <= t) lo = mid; else hi = mid - 1;
+// Offsets of the problems of a batched build (the union mesh of
+// ph_mesh_create_batch), one thread per problem.  Problem p owns tets
+// [toff[p], toff[p+1]); its faces, multipliers and CSR entries are
+// contiguous, and start at: the face of its first tet's first local face
+// (always a first occurrence), the multiplier of the first non-Neumann face at
+// or after it (Neumann faces have none; the walk may run into the next
+// problem's faces, whose first multiplier is then this problem's end, which is
+// also its start when it has no multiplier), and that row's first CSR entry.
+// An empty problem gets -1 (the host takes the next problem's offsets).
+__global__ void k_batch_offsets(const int4* __restrict__ tface, const int32_t* __restrict__ face_mult,
+                                const int32_t* __restrict__ rowptr, const int64_t* __restrict__ d_tot,
+                                const int64_t* __restrict__ toff, int32_t n, long long* __restrict__ out,
+                                const unsigned* status) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  long long f0 = -1, m0 = -1, z0 = -1;
+  if (toff[p + 1] > toff[p] && !failed(status)) {
+    const int64_t nF = d_tot[0], L = d_tot[1];
+    f0 = tface[toff[p]].x & PH_ID_MASK;
+    int64_t F = f0;
+    while (F < nF && face_mult[F] < 0) ++F;
+    m0 = F < nF ? face_mult[F] : L;
+    z0 = rowptr[m0];
   }
-  atomicAdd(&counts[3 * lo], 1ull);
-  const int l = face_mult[F];
-  if (l >= 0) {
-    atomicAdd(&counts[3 * lo + 1], 1ull);
-    atomicAdd(&counts[3 * lo + 2], (unsigned long long)(rowptr[l + 1] - rowptr[l]));
-  }
+  out[3 * p] = f0;
+  out[3 * p + 1] = m0;
+  out[3 * p + 2] = z0;
 }
 
-// Hook of a batched build: the per-problem counts, computed before the
+// Hook of a batched build: the per-problem offsets, computed before the
 // build's one synchronisation and read with it.
 struct BatchCounts {
   const int64_t* d_toff;  // n + 1 tet offsets (device)
   int32_t n;
-  unsigned long long* d_counts;  // 3n, zeroed by the caller
-  unsigned long long* h_counts;  // 3n (host)
+  long long* d_counts;  // 3n: first face, multiplier, CSR entry of each problem
+  long long* h_counts;  // 3n (host)
 };
 
 // Synchronise and read n device int64 counters and the status word.
@@ -542,15 +613,20 @@ static ph_status read_counters(const int64_t* d_tot, int n, unsigned* d_status, 
 #define PH_CU(expr, what) PH_TRY(cuda_status((expr), what))
 
 static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet, int64_t nE, const int32_t* neumann,
-                            int64_t nN, cudaStream_t s, ph_mesh** out, const BatchCounts* bc);
+                            int64_t nN, cudaStream_t s, ph_mesh** out, const BatchCounts* bc, bool dw = false);
 
 extern "C" ph_status ph_mesh_create(const double* coord, int64_t nC, const int32_t* tet, int64_t nE,
                                     const int32_t* neumann, int64_t nN, void* stream, ph_mesh** out) {
   return mesh_build(coord, nC, tet, nE, neumann, nN, (cudaStream_t)stream, out, nullptr);
 }
 
+extern "C" ph_status ph_mesh_create_dw(const double* coord, int64_t nC, const int32_t* tet, int64_t nE,
+                                       const int32_t* neumann, int64_t nN, void* stream, ph_mesh** out) {
+  return mesh_build(coord, nC, tet, nE, neumann, nN, (cudaStream_t)stream, out, nullptr, true);
+}
+
 static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet, int64_t nE, const int32_t* neumann,
-                            int64_t nN, cudaStream_t s, ph_mesh** out, const BatchCounts* bc) {
+                            int64_t nN, cudaStream_t s, ph_mesh** out, const BatchCounts* bc, bool dw) {
   if (!out) return PH_ERR_ARG;
   *out = nullptr;
   if (nE < 0 || nC < 0 || nN < 0 || (nE > 0 && (!coord || !tet)) || (nN > 0 && !neumann)) return PH_ERR_ARG;
@@ -648,7 +724,7 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
     {
       KernelTimer kt("k_face_fill", s, 2);
       k_face_fill<<<grid_for(nE + nN), kThreads, 0, s>>>(m->tet, nE, nC, neumann, nN, sub, start, cnt, entries,
-                                                         mate, m->coord, m->geo, m->status);
+                                                         mate, m->coord, m->geo, dw, m->status);
       PH_CU(launched(), "k_face_fill");
     }
     {
@@ -692,12 +768,12 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
                                        m->face_area, m->status);
     PH_CU(launched(), "k_row_fill");
   }
-  if (bc && bc->n > 0 && nFmax > 0) {  // per-problem counts of a batched build
-    k_batch_counts<<<gF, kThreads, 0, s>>>(m->face_tet, m->face_mult, m->rowptr, d_tot, nFmax, bc->d_toff, bc->n,
-                                           bc->d_counts, m->status);
-    PH_CU(launched(), "k_batch_counts");
-    PH_CU(cudaMemcpyAsync(bc->h_counts, bc->d_counts, sizeof(unsigned long long) * 3 * bc->n,
-                          cudaMemcpyDeviceToHost, s), "copy");
+  if (bc && bc->n > 0) {  // per-problem offsets of a batched build
+    k_batch_offsets<<<grid_for(bc->n), kThreads, 0, s>>>(m->tface, m->face_mult, m->rowptr, d_tot, bc->d_toff, bc->n,
+                                                         bc->d_counts, m->status);
+    PH_CU(launched(), "k_batch_offsets");
+    PH_CU(cudaMemcpyAsync(bc->h_counts, bc->d_counts, sizeof(long long) * 3 * bc->n, cudaMemcpyDeviceToHost, s),
+          "copy");
   }
   // the one synchronisation: counts and the first error of any kernel
   PH_TRY(read_counters(d_tot, 3, m->status, s, tot, &bits));
@@ -713,6 +789,7 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
   m->nFi = 4 * nE - m->nF;
   m->nFn = m->nF - m->L;
   m->nFd = m->nF - m->nFi - m->nFn;
+  m->geo_dw = dw;
   *out = m;
   return PH_OK;
 
@@ -941,7 +1018,7 @@ extern "C" ph_status ph_mesh_create_batch(int32_t n, const double* const* coord,
   Carve ic;
   const size_t o_coord = ic.take<double>(3 * nCu), o_tet = ic.take<int4>(nEu), o_nb = ic.take<int32_t>(3 * nNu);
   const size_t o_src = ic.take<UnionSources>(n), o_off = ic.take<int64_t>(3 * (n + 1));
-  const size_t o_cnt = ic.take<unsigned long long>(3 * n);
+  const size_t o_cnt = ic.take<long long>(3 * n);
   void* in = nullptr;
   cudaError_t e = alloc_bytes(&in, ic.bytes, s);
   if (e != cudaSuccess) return cuda_status(e, "alloc batch inputs");
@@ -950,7 +1027,7 @@ extern "C" ph_status ph_mesh_create_batch(int32_t n, const double* const* coord,
   int32_t* nb_u = Carve::at<int32_t>(in, o_nb);
   UnionSources* d_src = Carve::at<UnionSources>(in, o_src);
   int64_t* d_off = Carve::at<int64_t>(in, o_off);  // toff, noff, voff
-  unsigned long long* d_cnt = Carve::at<unsigned long long>(in, o_cnt);
+  long long* d_cnt = Carve::at<long long>(in, o_cnt);
   std::vector<int64_t> offs;
   offs.insert(offs.end(), toff.begin(), toff.end());
   offs.insert(offs.end(), noff.begin(), noff.end());
@@ -962,7 +1039,6 @@ extern "C" ph_status ph_mesh_create_batch(int32_t n, const double* const* coord,
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_src, src.data(), sizeof(UnionSources) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_off, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * 3 * n, s);
   if (e == cudaSuccess && nEu + nNu > 0) {
     k_union_inputs<<<grid_for(nEu + nNu), kThreads, 0, s>>>(d_src, d_off, d_off + (n + 1), d_off + 2 * (n + 1), n,
                                                           nEu, nNu, tet_u, nb_u);
@@ -972,21 +1048,28 @@ extern "C" ph_status ph_mesh_create_batch(int32_t n, const double* const* coord,
     free_async(in, s);
     return cuda_status(e, "ph_mesh_create_batch inputs");
   }
-  std::vector<unsigned long long> cnt(3 * (size_t)n, 0);
+  std::vector<long long> cnt(3 * (size_t)n, -1);
   BatchCounts bc{d_off, n, d_cnt, cnt.data()};
   ph_mesh* u = nullptr;
   ph_status st = mesh_build(coord_u, nCu, reinterpret_cast<const int32_t*>(tet_u), nEu, nNu > 0 ? nb_u : nullptr,
                             nNu, s, &u, &bc);
   free_async(in, s);
   if (st != PH_OK) return st;
-  // per-problem face, multiplier and CSR offsets from the counts
+  // per-problem face, multiplier and CSR offsets; an empty problem starts
+  // where the next one does
   std::vector<int64_t> foff(n + 1, 0), moff(n + 1, 0), zoff(n + 1, 0);
-  for (int32_t p = 0; p < n; ++p) {
-    foff[p + 1] = foff[p] + (int64_t)cnt[3 * p];
-    moff[p + 1] = moff[p] + (int64_t)cnt[3 * p + 1];
-    zoff[p + 1] = zoff[p] + (int64_t)cnt[3 * p + 2];
+  foff[n] = u->nF;
+  moff[n] = u->L;
+  zoff[n] = u->nnz;
+  bool ordered = true;
+  for (int32_t p = n - 1; p >= 0; --p) {
+    const bool empty = cnt[3 * p] < 0;
+    foff[p] = empty ? foff[p + 1] : cnt[3 * p];
+    moff[p] = empty ? moff[p + 1] : cnt[3 * p + 1];
+    zoff[p] = empty ? zoff[p + 1] : cnt[3 * p + 2];
+    ordered = ordered && foff[p] <= foff[p + 1] && moff[p] <= moff[p + 1] && zoff[p] <= zoff[p + 1];
   }
-  if (foff[n] != u->nF || moff[n] != u->L || zoff[n] != u->nnz) {
+  if (!ordered || foff[0] != 0 || moff[0] != 0 || zoff[0] != 0) {
     mesh_free(u, s);
     return PH_ERR_ARG;
   }

@@ -47,6 +47,7 @@ struct ph_mesh {
   int32_t* colind;     // nnz
   int32_t* rowdiag;    // L
   unsigned int* status;  // device status word: bit s set for ph_status s
+  bool geo_dw;           // geo holds the double-word record (ph_mesh_create_dw)
 };
 
 namespace ph {
