@@ -101,7 +101,9 @@ def test_adjoint_matches_oracle(ph, case, precond):
     else:
         p = meshgen.problem(case)
         p.c = 0.3
-    U_obs = obs_field(ph, p, 51)
+    # the observation: the oracle's own forward solve at another coefficient
+    U_obs = oracle.pipeline(p.coord, p.tet, meshgen.lognormal_field(p.nE, 51), p.c, p.f, p.uD, p.gN,
+                            p.neumann if p.neumann.size else None)["U"]
     a = meshgen.lognormal_field(p.nE, 5)
     s = Setup(ph, p, a, U_obs)
     s.precond = precond

@@ -10,14 +10,14 @@ Cases: every mesh of the fp64 parity tests (Listing 1 with and without mixed
 boundary data, Kuhn cubes, shuffled and degree-sorted meshes, the lognormal
 and jittered checkerboard workloads at small size), a soup of random
 isolated elements of graded flatness (slivers included) with diffusion- and
-reaction-dominated coefficients, and sampled rows of the full-size lognormal
-workload."""
+reaction-dominated coefficients.  The full-size workloads (every value of the
+3.36M- and 17.9M-tet meshes) are checked in test_gpu_fullsize.py."""
 import numpy as np
 import pytest
 
 import meshgen
 import oracle
-from tests.test_gpu_parity import CASES, assert_values_close, cu, host, make_case, run_oracle
+from tests.test_gpu_parity import CASES, assert_values_close, cu, host, make_case, oracle_face_data, run_oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -67,7 +67,7 @@ def assert_close_to_f64(g):
 def test_dw_assembly_parity(ph, name):
     p = make_case(name)
     g = run_both(ph, p)
-    o = run_oracle(p, f=g["f"], uD=g["uD"], gN=g["gN"])
+    o = run_oracle(p)
     assert_values_close({"values": g["dw"]["values"], "rhs": g["dw"]["rhs"]}, o)
     assert_close_to_f64(g)
     g["mesh"].close()
@@ -82,7 +82,8 @@ def test_dw_factor_recovery_parity(ph, name):
     lam = np.random.default_rng(2).standard_normal(L)
     u = g["mesh"].recover_factored(g["dw"]["factor_d"], p.c, cu(g["f"], torch.float64), cu(lam, torch.float64),
                                    None if g["gN"] is None else cu(g["gN"], torch.float64))
-    Uo = oracle.recover(p.coord, p.tet, fc, fm, p.a, p.c, g["f"], lam, g["gN"])
+    fo, _, gNo = oracle_face_data(p, fc)
+    Uo = oracle.recover(p.coord, p.tet, fc, fm, p.a, p.c, fo, lam, gNo)
     scale = np.abs(Uo).max(axis=1, keepdims=True)
     assert np.all(np.abs(host(u) - Uo) <= 1e-12 * scale)
     g["mesh"].close()
@@ -136,7 +137,7 @@ def test_dw_element_soup_against_oracle(ph, c):
     a = 10.0 ** np.random.default_rng(5).uniform(0, 4, tet.shape[0])
     p = meshgen.Problem("soup", coord, tet, a, c, lambda x: meshgen.sin_source(x))
     g = run_both(ph, p)
-    o = run_oracle(p, f=g["f"])
+    o = run_oracle(p)
     assert_soup_close(p, g, o, "f64")
     assert_soup_close(p, g, o, "dw")
     g["mesh"].close()
@@ -155,7 +156,7 @@ def test_dw_fallback_elements(ph):
     a = 5.0 * h2 / np.random.default_rng(9).uniform(5, 10, tet.shape[0])
     p = meshgen.Problem("fallback", coord, tet, a, 5.0, lambda x: meshgen.sin_source(x))
     g = run_both(ph, p)
-    o = run_oracle(p, f=g["f"])
+    o = run_oracle(p)
     assert_soup_close(p, g, o, "dw")
     for k in ("values", "rhs", "factor"):
         assert np.array_equal(g["dw"][k].view(np.uint64), g["f64"][k].view(np.uint64)), k
@@ -170,7 +171,7 @@ def test_dw_large_coefficients(ph):
     a = 10.0 ** np.random.default_rng(10).uniform(8, 14, tet.shape[0])
     p = meshgen.Problem("large", coord, tet, a, 0.5, lambda x: meshgen.sin_source(x))
     g = run_both(ph, p)
-    o = run_oracle(p, f=g["f"])
+    o = run_oracle(p)
     assert_soup_close(p, g, o, "f64")
     assert_soup_close(p, g, o, "dw")
     assert_close_to_f64(g)
@@ -207,10 +208,10 @@ def test_dw_mesh_parity(ph, name):
     from tests.test_gpu_parity import assert_connectivity_equal
     p = make_case(name)
     g = dw_mesh_run(ph, p)
-    o = run_oracle(p, f=g["f"], uD=g["uD"], gN=g["gN"])
+    o = run_oracle(p)
     assert_connectivity_equal(g, o)
     assert_values_close(g, o)
-    Uo = oracle.recover(p.coord, p.tet, o["fc"], o["csr"]["face_mult"], p.a, p.c, g["f"], g["lam"], g["gN"])
+    Uo = oracle.recover(p.coord, p.tet, o["fc"], o["csr"]["face_mult"], p.a, p.c, o["f"], g["lam"], o["gN"])
     assert np.all(np.abs(g["U"] - Uo) <= 1e-12 * np.abs(Uo).max(axis=1, keepdims=True))
     q = ph.Mesh(cu(p.coord, torch.float64), cu(p.tet, torch.int32),
                 cu(p.neumann, torch.int32) if p.neumann.size else None)
@@ -228,7 +229,7 @@ def test_dw_mesh_flat_elements_fall_back(ph):
     a = 10.0 ** np.random.default_rng(12).uniform(0, 4, tet.shape[0])
     p = meshgen.Problem("soup", coord, tet, a, 0.3, lambda x: meshgen.sin_source(x))
     g = dw_mesh_run(ph, p)
-    o = run_oracle(p, f=g["f"])
+    o = run_oracle(p)
     assert_soup_close(p, {"dw": g}, o, "dw")
     g["mesh"].close()
 
@@ -244,49 +245,3 @@ def test_dw_mesh_refuses_fp64_record_entry_points(ph):
             call()
         assert e.value.name == "PH_ERR_ARG"
     m.close()
-
-
-def full_size_sampled(ph, name, geometry):
-    """The full-size workload in the launch configuration bench.py times for
-    the variant: 2000 sampled rows of H and their rhs entries (1e-12, as the
-    fp64 path), and 2000 sampled element recoveries from the variant's
-    element factor with a random Lambda.  The factor carries the float pairs'
-    ~1e-14 relative error (fp64's: ~1e-16), and a random Lambda makes the
-    recovery's terms cancel (U = z'sum/(c|T|) - 3 (Qf/9) z'), so the recovery
-    is held to 2e-12 of the element's largest value here: the largest ratio
-    measured on the 17.9M-tet jittered mesh was 1.22e-12 (printed)."""
-    from tests.test_gpu_fullsize import check_sampled_rows
-    from tests.test_gpu_fullsize import element_inputs
-    p = meshgen.problem(name)
-    dev = torch.device("cuda")
-    mesh = ph.Mesh(torch.as_tensor(p.coord, device=dev), torch.as_tensor(p.tet, device=dev), geometry=geometry)
-    fc = {k: v.cpu().numpy() for k, v in mesh.faces().items()}
-    f = np.asarray(p.f(fc["face_centroid"]), np.float64)
-    rowptr, colind = mesh.csr_pattern()
-    a_d, f_d = torch.as_tensor(p.a, device=dev), torch.as_tensor(f, device=dev)
-    values, rhs, factor = mesh.assemble(a_d, p.c, f_d, factor=True, variant="dw")
-    lam = np.random.default_rng(3).standard_normal(mesh.L)
-    uf = mesh.recover_factored(factor, p.c, f_d, torch.as_tensor(lam, device=dev))
-    mesh.check()
-    g = {"info": dict(mesh.info), "fc": fc, "f": f, "rowptr": rowptr.cpu().numpy(), "colind": colind.cpu().numpy(),
-         "values": values.cpu().numpy(), "rhs": rhs.cpu().numpy(), "lam": lam, "U": uf.cpu().numpy(),
-         "U_factored": uf.cpu().numpy()}
-    mesh.close()
-    check_sampled_rows(p, g, np.random.default_rng(17))
-    rng = np.random.default_rng(18)
-    fm = g["fc"]["face_mult"]
-    worst = 0.0
-    for t in rng.choice(p.nE, 2000, replace=False):
-        P, f4, sig, Fk = element_inputs(p, g, t)
-        U = oracle.tet_recover(P, p.a[t], p.c, f4, sig, g["lam"][fm[Fk]])
-        worst = max(worst, float(np.abs(g["U"][t] - U).max() / np.abs(U).max()))
-    print(f"{name} ({geometry} mesh): worst recovery error over 2000 sampled elements {worst:.3e} of max |U|")
-    assert worst <= 2e-12
-
-
-def test_dw_full_size_lognormal(ph):
-    full_size_sampled(ph, "lognormal_3m", "f64")
-
-
-def test_dw_full_size_jitter_checker_dw_mesh(ph):
-    full_size_sampled(ph, "jitter_checker_18m", "dw")

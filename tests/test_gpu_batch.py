@@ -177,21 +177,24 @@ def test_batched_recovery_in_the_graph(ph):
            [c.rhs for c in cases], factor=[c.factor for c in cases], uD_face=[c.uD for c in cases],
            gN_face=[c.gN for c in cases])
     rng = np.random.default_rng(21)
-    lam = [cu(rng.standard_normal(c.mesh.L)) for c in cases]
+    lam_h = [rng.standard_normal(c.mesh.L) for c in cases]
+    lam = [cu(x) for x in lam_h]
     us = [torch.full((c.mesh.nE, 4), np.nan, dtype=torch.float64, device="cuda") for c in cases]
     b.bind_recovery(lam, us)
     n0 = ph.ph_launch_count()
     b.graph_launch()
     torch.cuda.synchronize()
     assert ph.ph_launch_count() - n0 == 3
-    for p, c, l, u in zip(probs, cases, lam, us):
+    for p, c, l, lh, u in zip(probs, cases, lam, lam_h, us):
         v, r, fa = c.ref
         ref = c.mesh.recover_factored(fa, c.c, c.f, l, c.gN)
         assert torch.equal(u, ref), p.name
+        # the oracle on its own faces, face data and the host copy of Lambda
         fc = oracle.faces(p.tet, p.nC, p.neumann if p.neumann.size else None)
         fm, _ = oracle.multipliers(fc["face_kind"])
-        Uo = oracle.recover(p.coord, p.tet, fc, fm, p.a, c.c, c.f.cpu().numpy(), l.cpu().numpy(),
-                            None if c.gN is None else c.gN.cpu().numpy())
+        cen = oracle.face_centroids(p.coord, fc["face_vtx"])
+        gN = None if p.gN is None else np.asarray(p.gN(cen), np.float64)
+        Uo = oracle.recover(p.coord, p.tet, fc, fm, p.a, c.c, np.asarray(p.f(cen), np.float64), lh, gN)
         scale = np.abs(Uo).max(axis=1, keepdims=True)
         assert np.all(np.abs(u.cpu().numpy() - Uo) <= 1e-12 * scale), p.name
     b.bind_recovery(None, None)  # back to two launches

@@ -2,12 +2,20 @@
 times (the same entry points and kernels, grids sized by the element count).
 
 - lognormal_3m (3,359,232 tets) and jitter_checker_18m (17,915,904 tets):
-  connectivity and CSR pattern compared bit-exactly with the oracle over the
-  whole mesh;
+  connectivity, CSR pattern and face centroids compared bit-exactly with the
+  oracle over the whole mesh;
+- every H value, rhs entry and recovered element value compared with the
+  oracle's assembly and recovery of the whole mesh (its element loops on all
+  host cores, bit-identical to one thread), for the fp64 path and for the
+  double-word variant on the jittered mesh;
 - H rows and rhs entries of 2000 sampled faces, and the recovery of 2000
-  sampled elements, compared with the oracle's per-element evaluation;
+  sampled elements, also compared with the oracle's per-element entry points;
 - properties that hold at any size: H symmetric with a positive diagonal,
   nnz = nF + 12 nE for an all-Dirichlet mesh, 12 m^2 4^k boundary faces.
+
+Every oracle input comes from the workload generator, a seeded generator or
+the oracle itself (its own faces and face centroids); the GPU side evaluates
+f at the centroids the library exports.
 """
 import numpy as np
 import pytest
@@ -20,6 +28,7 @@ pytestmark = pytest.mark.gpu
 
 VAL_RTOL = 1e-12
 NSAMPLE = 2000
+LAM_SEED = 3
 
 
 @pytest.fixture(scope="module")
@@ -37,57 +46,125 @@ def _host(t):
     return t.cpu().numpy()
 
 
-def run_full(ph, p):
+_ORACLE = {}
+
+
+def oracle_data(p):
+    """The oracle's faces, multipliers, CSR pattern, face centroids and f, and
+    its assembly and recovery (seeded random Lambda) of the whole mesh; kept
+    for the module's next test on the same workload."""
+    if p.name not in _ORACLE:
+        _ORACLE.clear()
+        fc = oracle.faces(p.tet, p.nC)
+        fm, L = oracle.multipliers(fc["face_kind"])
+        rowptr, colind = oracle.csr_pattern(fc["tet_face"], fm, L)
+        csr = dict(face_mult=fm, L=L, rowptr=rowptr, colind=colind)
+        cen = oracle.face_centroids(p.coord, fc["face_vtx"])
+        f = np.asarray(p.f(cen), np.float64)
+        values, rhs, rhs_abs = oracle.assemble(p.coord, p.tet, fc, csr, p.a, p.c, f)
+        lam = np.random.default_rng(LAM_SEED).standard_normal(L)
+        U = oracle.recover(p.coord, p.tet, fc, fm, p.a, p.c, f, lam)
+        _ORACLE[p.name] = dict(fc=fc, csr=csr, cen=cen, f=f, values=values, rhs=rhs, rhs_abs=rhs_abs, lam=lam,
+                               U=U)
+    return _ORACLE[p.name]
+
+
+def run_full(ph, p, geometry="f64", variant="f64"):
+    """The full-size path on the GPU: mesh build, assembly with the element
+    factor, recovery with and (fp64 record) without the factor."""
     dev = torch.device("cuda")
-    mesh = ph.Mesh(torch.as_tensor(p.coord, device=dev), torch.as_tensor(p.tet, device=dev))
+    mesh = ph.Mesh(torch.as_tensor(p.coord, device=dev), torch.as_tensor(p.tet, device=dev), geometry=geometry)
     fc = {k: _host(v) for k, v in mesh.faces().items()}
     f = np.asarray(p.f(fc["face_centroid"]), np.float64)
     rowptr, colind = mesh.csr_pattern()
     a_d, f_d = torch.as_tensor(p.a, device=dev), torch.as_tensor(f, device=dev)
-    values, rhs, factor = mesh.assemble(a_d, p.c, f_d, factor=True)
-    lam = np.random.default_rng(3).standard_normal(mesh.L)
+    values, rhs, factor = mesh.assemble(a_d, p.c, f_d, factor=True, variant=variant)
+    lam = np.random.default_rng(LAM_SEED).standard_normal(mesh.L)
     lam_d = torch.as_tensor(lam, device=dev)
-    u = mesh.recover(a_d, p.c, f_d, lam_d)
+    u = mesh.recover(a_d, p.c, f_d, lam_d) if geometry == "f64" else None
     uf = mesh.recover_factored(factor, p.c, f_d, lam_d)
     mesh.check()
-    out = dict(info=dict(mesh.info), fc=fc, f=f, lam=lam, rowptr=_host(rowptr), colind=_host(colind),
-               values=_host(values), rhs=_host(rhs), U=_host(u), U_factored=_host(uf))
+    out = dict(info=dict(mesh.info), fc=fc, rowptr=_host(rowptr), colind=_host(colind), values=_host(values),
+               rhs=_host(rhs), U=None if u is None else _host(u), U_factored=_host(uf))
     mesh.close()
     return out
 
 
 def check_connectivity(p, g):
-    o = oracle.faces(p.tet, p.nC)
+    o = oracle_data(p)
     for k in ("tet_face", "face_tet", "face_vtx", "face_kind"):
-        assert np.array_equal(g["fc"][k], o[k]), k
-    fm, L = oracle.multipliers(o["face_kind"])
-    assert np.array_equal(g["fc"]["face_mult"], fm)
-    rowptr, colind = oracle.csr_pattern(o["tet_face"], fm, L)
-    assert np.array_equal(g["rowptr"], rowptr)
-    assert np.array_equal(g["colind"], colind)
+        assert np.array_equal(g["fc"][k], o["fc"][k]), k
+    assert np.array_equal(g["fc"]["face_mult"], o["csr"]["face_mult"])
+    assert np.array_equal(g["rowptr"], o["csr"]["rowptr"])
+    assert np.array_equal(g["colind"], o["csr"]["colind"])
+    assert np.array_equal(g["fc"]["face_centroid"], o["cen"])
 
 
-def element_inputs(p, g, t):
-    tf = g["fc"]["tet_face"][t]
+def recovery_terms(p, o):
+    """Per element, the magnitude of the terms the recovery sums,
+    (1/(c|T|)) sum_m (|T|/4 |f_m| + |F_m| |Lambda_m|): the scale of the
+    rounding in U = z'sum/(c|T|) - 3 (Qf/9) z' (numpy, from the mesh)."""
+    P = p.coord[p.tet]
+    vol = np.abs(np.linalg.det(P[:, 1:] - P[:, :1])) / 6.0
+    x = p.coord[o["fc"]["face_vtx"]]
+    area = 0.5 * np.linalg.norm(np.cross(x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]), axis=1)
+    F = o["fc"]["tet_face"] & 0x7FFFFFFF
+    z = vol[:, None] / 4 * np.abs(o["f"][F]) + area[F] * np.abs(o["lam"][o["csr"]["face_mult"][F]])
+    return z.sum(axis=1) / (p.c * vol)
+
+
+def check_all_values(p, g, what, u_rtol=1e-12):
+    """Every H value (1e-12 of itself: an off-diagonal entry has one addend,
+    the diagonal's two addends are positive), every rhs entry (1e-12 of the
+    sum of its addends' magnitudes) and every recovered value (u_rtol of the
+    element's largest), against the oracle's whole-mesh assembly and
+    recovery.  Prints the worst ratios, and for the worst recovered element
+    how far its terms exceed its values."""
+    o = oracle_data(p)
+    err = np.abs(g["values"] - o["values"])
+    ratio = float((err / np.abs(o["values"])).max())
+    bad = int(np.count_nonzero(err > VAL_RTOL * np.abs(o["values"])))
+    rerr = float((np.abs(g["rhs"] - o["rhs"]) / np.maximum(o["rhs_abs"], 1e-300)).max())
+    scale = np.abs(o["U"]).max(axis=1)
+    terms = recovery_terms(p, o)
+    worst = {}
+    for k in ("U", "U_factored"):
+        if g[k] is None:
+            continue
+        e = np.abs(g[k] - o["U"]).max(axis=1) / scale
+        t = int(np.argmax(e))
+        worst[k] = float(e[t])
+        print(f"{p.name} {what} {k}: worst {e[t]:.3g} of max|U| at element {t} (terms {terms[t] / scale[t]:.3g} x "
+              f"max|U|); elements above 1e-13: {int(np.count_nonzero(e > 1e-13))} of {e.size}")
+    print(f"{p.name} {what}: {o['values'].size} H values, worst relative error {ratio:.3g} ({bad} above "
+          f"{VAL_RTOL:g}); rhs worst {rerr:.3g} of the addends' magnitudes")
+    assert bad == 0, (bad, ratio)
+    assert rerr <= 1e-12
+    for k, w in worst.items():
+        assert w <= u_rtol, (k, w)
+
+
+def element_inputs(p, o, t):
+    tf = o["fc"]["tet_face"][t]
     F = tf & 0x7FFFFFFF
     sig = np.where(tf < 0, -1, 1)
-    return p.coord[p.tet[t]], g["f"][F], sig, F
+    return p.coord[p.tet[t]], o["f"][F], sig, F
 
 
 def check_sampled_rows(p, g, rng):
     """Rows of H and rhs entries of sampled faces, rebuilt from the oracle's
     element blocks of the face's one or two tets."""
-    fc, rowptr, colind = g["fc"], g["rowptr"], g["colind"]
-    faces = rng.choice(g["info"]["nF"], NSAMPLE, replace=False)
-    fm = fc["face_mult"]
-    for F in faces:
+    o = oracle_data(p)
+    fc, fm = o["fc"], o["csr"]["face_mult"]
+    rowptr, colind = g["rowptr"], g["colind"]
+    for F in rng.choice(g["info"]["nF"], NSAMPLE, replace=False):
         l = fm[F]
         row = {}
         rhs, rhs_abs = 0.0, 0.0
         for T in fc["face_tet"][F]:
             if T < 0:
                 continue
-            P, f4, sig, Fk = element_inputs(p, g, T)
+            P, f4, sig, Fk = element_inputs(p, o, T)
             S, gv = oracle.tet_local(P, p.a[T], p.c, f4, sig)
             k = int(np.nonzero(Fk == F)[0][0])
             for m in range(4):
@@ -102,14 +179,15 @@ def check_sampled_rows(p, g, rng):
         assert abs(g["rhs"][l] - rhs) <= 1e-12 * rhs_abs + 1e-300
 
 
-def check_sampled_recovery(p, g, rng):
-    tets = rng.choice(p.nE, NSAMPLE, replace=False)
-    fm = g["fc"]["face_mult"]
-    for t in tets:
-        P, f4, sig, Fk = element_inputs(p, g, t)
-        U = oracle.tet_recover(P, p.a[t], p.c, f4, sig, g["lam"][fm[Fk]])
-        assert np.all(np.abs(g["U"][t] - U) <= 1e-12 * np.abs(U).max())
-        assert np.all(np.abs(g["U_factored"][t] - U) <= 1e-12 * np.abs(U).max())
+def check_sampled_recovery(p, g, rng, u_rtol=1e-12):
+    o = oracle_data(p)
+    fm = o["csr"]["face_mult"]
+    for t in rng.choice(p.nE, NSAMPLE, replace=False):
+        P, f4, sig, Fk = element_inputs(p, o, t)
+        U = oracle.tet_recover(P, p.a[t], p.c, f4, sig, o["lam"][fm[Fk]])
+        for k in ("U", "U_factored"):
+            if g[k] is not None:
+                assert np.all(np.abs(g[k][t] - U) <= u_rtol * np.abs(U).max()), (k, t)
 
 
 def check_properties(p, g, m, k):
@@ -140,6 +218,10 @@ def test_lognormal_3m_connectivity(lognormal):
     check_connectivity(*lognormal)
 
 
+def test_lognormal_3m_all_values(lognormal):
+    check_all_values(*lognormal, "f64")
+
+
 def test_lognormal_3m_sampled_rows_and_recovery(lognormal):
     p, g = lognormal
     rng = np.random.default_rng(11)
@@ -151,8 +233,24 @@ def test_lognormal_3m_properties(lognormal):
     check_properties(*lognormal, m=3, k=4)
 
 
+def test_lognormal_3m_double_word_variant(ph, lognormal):
+    """ph_assemble_dw on the fp64 record of the 3.36M-tet mesh: every H value
+    and rhs entry at the fp64 path's 1e-12; the recovery from its element
+    factor (which carries the float pairs' ~1e-14 relative error, against
+    fp64's ~1e-16, into the recovery's cancelling terms) at 2e-12 of each
+    element's largest value."""
+    p, _ = lognormal
+    g = run_full(ph, p, "f64", "dw")
+    g["U"] = None
+    check_all_values(p, g, "dw", u_rtol=2e-12)
+
+
 def test_jitter_checker_18m_connectivity(jitter):
     check_connectivity(*jitter)
+
+
+def test_jitter_checker_18m_all_values(jitter):
+    check_all_values(*jitter, "f64")
 
 
 def test_jitter_checker_18m_sampled_rows_and_recovery(jitter):
@@ -164,3 +262,14 @@ def test_jitter_checker_18m_sampled_rows_and_recovery(jitter):
 
 def test_jitter_checker_18m_properties(jitter):
     check_properties(*jitter, m=1, k=6)
+
+
+def test_jitter_checker_18m_double_word_mesh(ph, jitter):
+    """ph_mesh_create_dw + ph_assemble_dw + ph_recover_factored on the
+    17.9M-tet jittered mesh, the variant bench.py times: connectivity
+    bit-exact, every H value and rhs entry at 1e-12, the recovery from its
+    element factor at 2e-12 of each element's largest value (as above)."""
+    p, _ = jitter
+    g = run_full(ph, p, "dw", "dw")
+    check_connectivity(p, g)
+    check_all_values(p, g, "dw mesh", u_rtol=2e-12)

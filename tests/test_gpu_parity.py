@@ -74,14 +74,27 @@ def run_gpu(ph, p, a=None, lam=None, solve=False):
     return out
 
 
-def run_oracle(p, a=None, f=None, uD=None, gN=None, solve=False):
+def oracle_face_data(p, fc):
+    """f, u_D and g_N at the oracle's own face centroids.  The GPU side
+    evaluates them at the centroids the library exports, so each side derives
+    its inputs on its own (a test checks the two sets of centroids bit for
+    bit)."""
+    cen = oracle.face_centroids(p.coord, fc["face_vtx"])
+    f = np.asarray(p.f(cen), np.float64)
+    uD = None if p.uD is None else np.asarray(p.uD(cen), np.float64)
+    gN = None if p.gN is None else np.asarray(p.gN(cen), np.float64)
+    return f, uD, gN
+
+
+def run_oracle(p, a=None, solve=False):
     a = p.a if a is None else a
     fc = oracle.faces(p.tet, p.nC, p.neumann)
     fm, L = oracle.multipliers(fc["face_kind"])
     rowptr, colind = oracle.csr_pattern(fc["tet_face"], fm, L)
     csr = {"face_mult": fm, "L": L, "rowptr": rowptr, "colind": colind}
+    f, uD, gN = oracle_face_data(p, fc)
     values, rhs, rhs_abs = oracle.assemble(p.coord, p.tet, fc, csr, a, p.c, f, uD, gN)
-    out = dict(fc=fc, csr=csr, values=values, rhs=rhs, rhs_abs=rhs_abs)
+    out = dict(fc=fc, csr=csr, f=f, uD=uD, gN=gN, values=values, rhs=rhs, rhs_abs=rhs_abs)
     if solve:
         lam = oracle.solve(rowptr, colind, values, rhs)
         out.update(lam=lam, U=oracle.recover(p.coord, p.tet, fc, fm, a, p.c, f, lam, gN))
@@ -170,7 +183,7 @@ def make_case(name):
 def test_assembly_parity(ph, name):
     p = make_case(name)
     g = run_gpu(ph, p)
-    o = run_oracle(p, f=g["f"], uD=g["uD"], gN=g["gN"])
+    o = run_oracle(p)
     # the GPU's face centroids are the oracle's (same face tuples, same formula)
     cen_o = oracle.face_centroids(p.coord, o["fc"]["face_vtx"])
     assert np.array_equal(g["fc"]["face_centroid"], cen_o)
@@ -186,7 +199,8 @@ def test_recovery_parity_given_lambda(ph, name):
     fm, L = oracle.multipliers(fc["face_kind"])
     lam = np.random.default_rng(1).standard_normal(L)
     g = run_gpu(ph, p, lam=lam)
-    Uo = oracle.recover(p.coord, p.tet, fc, fm, p.a, p.c, g["f"], lam, g["gN"])
+    fo, _, gNo = oracle_face_data(p, fc)
+    Uo = oracle.recover(p.coord, p.tet, fc, fm, p.a, p.c, fo, lam, gNo)
     scale = np.abs(Uo).max(axis=1, keepdims=True)
     assert np.all(np.abs(g["U"] - Uo) <= 1e-12 * scale)
     assert np.all(np.abs(g["U_factored"] - Uo) <= 1e-12 * scale)
@@ -197,7 +211,7 @@ def test_recovery_parity_given_lambda(ph, name):
 def test_solve_and_recover_parity(ph, name):
     p = make_case(name)
     g = run_gpu(ph, p, solve=True)
-    o = run_oracle(p, f=g["f"], uD=g["uD"], gN=g["gN"], solve=True)
+    o = run_oracle(p, solve=True)
     assert g["relres"] <= 1e-13
     assert np.linalg.norm(g["lam"] - o["lam"]) <= SOLVE_RTOL * np.linalg.norm(o["lam"])
     assert np.linalg.norm(g["U"] - o["U"]) <= SOLVE_RTOL * np.linalg.norm(o["U"])
@@ -215,7 +229,7 @@ def test_refined_solve_parity(ph, name):
     both numbers are printed."""
     p = make_case(name)
     g = run_gpu(ph, p)
-    o = run_oracle(p, f=g["f"], uD=g["uD"], gN=g["gN"])
+    o = run_oracle(p)
     rowptr, colind = o["csr"]["rowptr"], o["csr"]["colind"]
     lam_o, _, _ = oracle.solve_refined(rowptr, colind, o["values"], o["rhs"])
     mesh = g["mesh"]
@@ -274,7 +288,7 @@ def test_single_tet_and_empty(ph):
     p = meshgen.Problem("one", np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float),
                         np.array([[0, 1, 2, 3]], np.int32), np.array([2.0]), 0.5, lambda x: meshgen.sin_source(x))
     g = run_gpu(ph, p)
-    o = run_oracle(p, f=g["f"])
+    o = run_oracle(p)
     assert_connectivity_equal(g, o)
     assert_values_close(g, o)
     g["mesh"].close()

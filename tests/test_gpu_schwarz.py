@@ -39,13 +39,22 @@ def cu(x):
 
 
 def system(ph, p):
+    """The mesh built on the GPU, and the oracle's assembled system on it
+    (face data at the oracle's own centroids): the solvers are tested on an
+    H and rhs that come from the oracle, whose CSR pattern is the library's
+    bit for bit.  Returns the mesh, the device system and its host copy."""
     neu = cu(p.neumann.astype(np.int32)) if p.neumann.size else None
     m = ph.Mesh(cu(p.coord), cu(p.tet.astype(np.int32)), neu)
-    cen = m.faces()["face_centroid"].cpu().numpy()
-    opt = lambda fn: None if fn is None else cu(np.asarray(fn(cen), np.float64))
-    values, rhs = m.assemble(cu(p.a), p.c, cu(np.asarray(p.f(cen), np.float64)), opt(p.uD), opt(p.gN))
+    fc = oracle.faces(p.tet, p.nC, p.neumann if p.neumann.size else None)
+    fm, L = oracle.multipliers(fc["face_kind"])
+    rp, ci = oracle.csr_pattern(fc["tet_face"], fm, L)
+    cen = oracle.face_centroids(p.coord, fc["face_vtx"])
+    opt = lambda fn: None if fn is None else np.asarray(fn(cen), np.float64)
+    va, b, _ = oracle.assemble(p.coord, p.tet, fc, {"face_mult": fm, "L": L, "rowptr": rp, "colind": ci}, p.a, p.c,
+                               opt(p.f), opt(p.uD), opt(p.gN))
     rowptr, colind = m.csr_pattern()
-    return m, values, rhs, rowptr, colind
+    assert np.array_equal(rowptr.cpu().numpy(), rp) and np.array_equal(colind.cpu().numpy(), ci)
+    return m, cu(va), cu(b), rowptr, colind, (rp, ci, va, b)
 
 
 CASES = ["sin_kuhn", "paper_mixed2", "lognormal_m3_k2", "jitter_checker_m1_k3"]
@@ -71,11 +80,11 @@ def make(name):
 @pytest.mark.parametrize("name", CASES)
 def test_schwarz_solve_matches_direct_solve(ph, name):
     p = make(name)
-    m, values, rhs, rowptr, colind = system(ph, p)
+    m, values, rhs, rowptr, colind, host_sys = system(ph, p)
     P = ph.Schwarz(m, values)
     rtol = 1e-12
     x, it, rr, _ = P.solve(values, rhs, rtol=rtol, maxit=20000)
-    rp, ci, va, b = rowptr.cpu().numpy(), colind.cpu().numpy(), values.cpu().numpy(), rhs.cpu().numpy()
+    rp, ci, va, b = host_sys
     ref, _, _ = oracle.solve_refined(rp, ci, va, b)
     x = x.cpu().numpy()
     H = sp.csr_matrix((va, ci, rp), shape=(m.L, m.L))
@@ -101,10 +110,10 @@ def test_refined_solve_reaches_fp64_accuracy(ph, name, precond):
     if precond == "jacobi" and name != "sin_kuhn" and name != "jitter_checker_m1_k3":
         pytest.skip("Jacobi on the two extreme cases only")
     p = make(name)
-    m, values, rhs, rowptr, colind = system(ph, p)
+    m, values, rhs, rowptr, colind, host_sys = system(ph, p)
     P = ph.Schwarz(m, values) if precond == "schwarz" else None
     x, steps, it, corr, _ = ph.solve_refined(m, values, rhs, P, tol=1e-15, inner_rtol=1e-8, maxit=200000)
-    rp, ci, va, b = rowptr.cpu().numpy(), colind.cpu().numpy(), values.cpu().numpy(), rhs.cpu().numpy()
+    rp, ci, va, b = host_sys
     ref, _, _ = oracle.solve_refined(rp, ci, va, b)
     err = np.linalg.norm(x.cpu().numpy() - ref) / np.linalg.norm(ref)
     print(f"{name} {precond}: refined in {steps} steps, {it} PCG iterations, correction {corr:.2e}, error {err:.2e}")
@@ -116,7 +125,7 @@ def test_refined_solve_reaches_fp64_accuracy(ph, name, precond):
 
 def test_schwarz_solve_repeatable(ph):
     p = make("lognormal_m3_k2")
-    m, values, rhs, _, _ = system(ph, p)
+    m, values, rhs, _, _, _ = system(ph, p)
     P = ph.Schwarz(m, values)
     x1, it1, _, _ = P.solve(values, rhs, rtol=1e-11)
     x2, it2, _, _ = P.solve(values, rhs, rtol=1e-11)
