@@ -84,7 +84,8 @@ E_INFLIGHT = 2
 TIMED_KERNELS = ("k_assemble", "zero_values", "k_recover_factored")
 # mesh-build kernels, timed in a separate short loop (their timers add host
 # work between the build's launches)
-BUILD_KERNELS = ("k_face_count", "k_face_fill", "k_face_match", "k_face_emit", "k_row_fill", "k_scan")
+BUILD_KERNELS = ("k_face_count", "k_face_fill", "k_face_match", "k_face_emit", "k_row_fill", "k_scan",
+                 "k_tet_geometry", "k_face_area")
 # sources that k_assemble (both variants) is compiled from
 ASSEMBLE_SOURCES = ("assemble.cu", "element.cuh", "fp64.cuh", "dw.cuh")
 
@@ -97,13 +98,10 @@ def assemble_sources_sha256(sources=ASSEMBLE_SOURCES):
     return h.hexdigest()
 
 
-def profile_figures(kernel="k_assemble"):
-    """Per-element figures of the committed ncu capture of a kernel (taken
-    on a smaller mesh of the lognormal recipe; the kernel's work and traffic
-    per element do not depend on the mesh size): DRAM bytes and FP64
-    instructions per element.  Empty when the kernel's sources changed after
-    the counters were taken."""
-    prof = os.path.join(ROOT, "profiles", f"{kernel}_lognormal_1m.txt")
+def profile_kv(name):
+    """key: value lines of a committed profile summary, or {} when it is
+    missing or the sources it names changed after the counters were taken."""
+    prof = os.path.join(ROOT, "profiles", name)
     try:
         kv = {}
         for line in open(prof):
@@ -114,12 +112,35 @@ def profile_figures(kernel="k_assemble"):
         return {}
     if kv.get("sources_sha256") != assemble_sources_sha256(tuple(kv.get("sources", "").split())):
         return {}
+    return kv
+
+
+def profile_figures(kernel="k_assemble"):
+    """Per-element figures of the committed ncu capture of a kernel (taken
+    on a smaller mesh of the lognormal recipe; the kernel's work and traffic
+    per element do not depend on the mesh size): DRAM bytes and FP64
+    instructions per element.  Empty when the kernel's sources changed after
+    the counters were taken."""
+    kv = profile_kv(f"{kernel}_lognormal_1m.txt")
     out = {}
     for key in ("dram_bytes_per_tet", "fp64_inst_per_tet", "fp32_inst_per_tet"):
         try:
             out[key] = float(kv[key])
         except (KeyError, ValueError):
             pass
+    return out
+
+
+def step_fp64_counts():
+    """FP64 instructions per element of every kernel of the step (ncu's
+    DFMA + DMUL + DADD counters of one build, assembly and recovery on the
+    995,328-tet lognormal mesh, divided by its element count), or {} when
+    the capture does not match the sources."""
+    kv = profile_kv("fp64_step_lognormal_1m.txt")
+    out = {}
+    for k, v in kv.items():
+        if k.startswith("fp64_per_tet "):
+            out[k.split(" ", 1)[1]] = float(v)
     return out
 
 
@@ -482,6 +503,7 @@ def gpu_arm(args, rank, world, local_rank):
             "frac": bpt * nE / asm_s / 1e9 / hbm_peak, "bytes_per_tet": bpt,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
         },
+        "roofline_step": step_roofline(nE, ms_per_step, fp64_peak_gops),
         "e2e": None if args.no_e2e else {"value": whole_job_rate(nE, world, e2e_ms), "unit": UNIT,
                                          "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                                          "api": "ph_assemble_host (pinned host buffers, one call per step)",
@@ -502,6 +524,21 @@ def gpu_arm(args, rank, world, local_rank):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.workload, budget_s=args.cpu_budget)
     return line
+
+
+def step_roofline(nE, step_ms, fp64_peak_gops):
+    """The whole step against the FP64 pipe: every FP64 instruction of the
+    step's kernels (per-element counts from the committed ncu capture) over
+    the step's time; null when the capture does not match the sources."""
+    counts = step_fp64_counts()
+    if not counts:
+        return None
+    per_tet = sum(counts.values())
+    g = per_tet * nE / (step_ms * 1e-3) / 1e9
+    return {"what": "all FP64 instructions of one step (mesh build, assembly, recovery) over the step time",
+            "bound": "alu", "achieved": g, "peak": fp64_peak_gops, "unit": "G FP64-op/s",
+            "frac": g / fp64_peak_gops, "fp64_inst_per_tet": per_tet, "per_kernel": counts,
+            "ops_source": "ncu FP64 instructions (DFMA+DADD+DMUL), profiles/fp64_step_lognormal_1m.txt"}
 
 
 def variant_report(v, nE, nC, nF, world, fp64_peak_gops, hbm_peak, f64_step_ms, f64_k_asm_ms):

@@ -7,7 +7,7 @@ times (the same entry points and kernels, grids sized by the element count).
 - every H value, rhs entry and recovered element value compared with the
   oracle's assembly and recovery of the whole mesh (its element loops on all
   host cores, bit-identical to one thread), for the fp64 path and for the
-  double-word variant on the jittered mesh;
+  double-word variant;
 - H rows and rhs entries of 2000 sampled faces, and the recovery of 2000
   sampled elements, also compared with the oracle's per-element entry points;
 - properties that hold at any size: H symmetric with a positive diagonal,
@@ -113,13 +113,23 @@ def recovery_terms(p, o):
     return z.sum(axis=1) / (p.c * vol)
 
 
-def check_all_values(p, g, what, u_rtol=1e-12):
+U_TERM_ULPS = 8
+EPS64 = 2.0 ** -53
+
+
+def check_all_values(p, g, what):
     """Every H value (1e-12 of itself: an off-diagonal entry has one addend,
     the diagonal's two addends are positive), every rhs entry (1e-12 of the
-    sum of its addends' magnitudes) and every recovered value (u_rtol of the
-    element's largest), against the oracle's whole-mesh assembly and
-    recovery.  Prints the worst ratios, and for the worst recovered element
-    how far its terms exceed its values."""
+    sum of its addends' magnitudes) and every recovered value, against the
+    oracle's whole-mesh assembly and recovery.
+
+    The recovery U = z'sum/(c|T|) - 3 (Qf/9) z' with a random Lambda (not a
+    solution of the system) cancels: at some elements its terms are 1e6-1e7
+    times the largest |U| (on the 17.9M-tet mesh, 7e7).  An fp64 evaluation
+    is then exact only to the rounding of the terms, so the bar is 1e-12 of
+    the element's largest |U| plus 8 ulp of the terms' magnitudes
+    (recovery_terms); the worst error measured is under one ulp of the terms,
+    for the fp64 path and the double-word variant alike (both printed)."""
     o = oracle_data(p)
     err = np.abs(g["values"] - o["values"])
     ratio = float((err / np.abs(o["values"])).max())
@@ -127,21 +137,23 @@ def check_all_values(p, g, what, u_rtol=1e-12):
     rerr = float((np.abs(g["rhs"] - o["rhs"]) / np.maximum(o["rhs_abs"], 1e-300)).max())
     scale = np.abs(o["U"]).max(axis=1)
     terms = recovery_terms(p, o)
-    worst = {}
+    bar = VAL_RTOL * scale + U_TERM_ULPS * EPS64 * terms
+    over = {}
     for k in ("U", "U_factored"):
         if g[k] is None:
             continue
-        e = np.abs(g[k] - o["U"]).max(axis=1) / scale
-        t = int(np.argmax(e))
-        worst[k] = float(e[t])
-        print(f"{p.name} {what} {k}: worst {e[t]:.3g} of max|U| at element {t} (terms {terms[t] / scale[t]:.3g} x "
-              f"max|U|); elements above 1e-13: {int(np.count_nonzero(e > 1e-13))} of {e.size}")
+        e = np.abs(g[k] - o["U"]).max(axis=1)
+        t = int(np.argmax(e / scale))
+        over[k] = int(np.count_nonzero(e > bar))
+        print(f"{p.name} {what} {k}: worst {e[t] / scale[t]:.3g} of max|U| at element {t}, whose terms are "
+              f"{terms[t] / scale[t]:.3g} x max|U|; worst {float((e / (EPS64 * terms)).max()):.3g} ulp of the "
+              f"terms; {int(np.count_nonzero(e > 1e-12 * scale))} of {e.size} elements above 1e-12 max|U|, "
+              f"{over[k]} above the bar")
     print(f"{p.name} {what}: {o['values'].size} H values, worst relative error {ratio:.3g} ({bad} above "
           f"{VAL_RTOL:g}); rhs worst {rerr:.3g} of the addends' magnitudes")
     assert bad == 0, (bad, ratio)
     assert rerr <= 1e-12
-    for k, w in worst.items():
-        assert w <= u_rtol, (k, w)
+    assert all(n == 0 for n in over.values()), over
 
 
 def element_inputs(p, o, t):
@@ -234,15 +246,13 @@ def test_lognormal_3m_properties(lognormal):
 
 
 def test_lognormal_3m_double_word_variant(ph, lognormal):
-    """ph_assemble_dw on the fp64 record of the 3.36M-tet mesh: every H value
-    and rhs entry at the fp64 path's 1e-12; the recovery from its element
-    factor (which carries the float pairs' ~1e-14 relative error, against
-    fp64's ~1e-16, into the recovery's cancelling terms) at 2e-12 of each
-    element's largest value."""
+    """ph_assemble_dw on the fp64 record of the 3.36M-tet mesh: every H value,
+    rhs entry and value recovered from its element factor, at the fp64
+    path's bars."""
     p, _ = lognormal
     g = run_full(ph, p, "f64", "dw")
     g["U"] = None
-    check_all_values(p, g, "dw", u_rtol=2e-12)
+    check_all_values(p, g, "dw")
 
 
 def test_jitter_checker_18m_connectivity(jitter):
@@ -267,9 +277,9 @@ def test_jitter_checker_18m_properties(jitter):
 def test_jitter_checker_18m_double_word_mesh(ph, jitter):
     """ph_mesh_create_dw + ph_assemble_dw + ph_recover_factored on the
     17.9M-tet jittered mesh, the variant bench.py times: connectivity
-    bit-exact, every H value and rhs entry at 1e-12, the recovery from its
-    element factor at 2e-12 of each element's largest value (as above)."""
+    bit-exact, every H value, rhs entry and recovered value at the fp64
+    path's bars."""
     p, _ = jitter
     g = run_full(ph, p, "dw", "dw")
     check_connectivity(p, g)
-    check_all_values(p, g, "dw mesh", u_rtol=2e-12)
+    check_all_values(p, g, "dw mesh")
