@@ -14,9 +14,7 @@
 #include <math.h>
 #include <string.h>
 
-#include <algorithm>
 #include <initializer_list>
-#include <mutex>
 #include <vector>
 
 
@@ -189,11 +187,14 @@ __global__ void k_face_count(const int4* __restrict__ tet, int64_t nE, int64_t n
 }
 
 // 2. scatter keys into buckets: entry = (v0, v1, v2, slot), slot = 4t+k for
-//    tet faces and 4nE+i for Neumann triples.  cnt counts down to 0.  (The
-//    element geometry runs beside it, on the build's second stream.)
+//    tet faces and 4nE+i for Neumann triples.  cnt counts down to 0.  The
+//    same thread then computes the tet's geometry record: the FP64-bound
+//    geometry and the latency-bound atomics and scattered stores overlap in
+//    the SM's warp scheduler.
 __global__ void k_face_fill(const int4* __restrict__ tet, int64_t nE, int64_t nC, const int32_t* __restrict__ nb,
                             int64_t nN, int sub, const int32_t* __restrict__ start, int32_t* __restrict__ cnt,
-                            int4* __restrict__ entries, int32_t* __restrict__ mate, unsigned* status) {
+                            int4* __restrict__ entries, int32_t* __restrict__ mate, const double* __restrict__ coord,
+                            double* __restrict__ geo, bool geo_dw, unsigned* status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (failed(status)) return;
   if (i < nE) {
@@ -207,6 +208,8 @@ __global__ void k_face_fill(const int4* __restrict__ tet, int64_t nE, int64_t nC
       entries[pos] = make_int4(s.x, s.y, s.z, (int)(4 * i + k));
     }
     reinterpret_cast<int4*>(mate)[i] = make_int4(-1, -1, -1, -1);  // no mate yet (boundary)
+    if (geo_dw) tet_geom_dw(coord, v, i, geo, status);
+    else tet_geom(coord, v, i, geo, status);
   } else if (i < nE + nN) {
     int3 f = neumann_tri(nb, i - nE);
     if (!valid_tri(f, nC)) return;
@@ -462,16 +465,18 @@ __device__ __forceinline__ int rank7(const int c[7], int x) {
 //    other three local faces (4-bit two's complement, m != k ascending).
 //    Row l(F) holds l(F) and the other non-Neumann faces of F's one or two
 //    tets (all distinct): 7 candidates with PH_NO_MULT for absent ones, put in
-//    order by a 16-comparator sorting network, all in registers.  (The face
-//    areas run beside it, on the build's second stream.)
+//    order by a 16-comparator sorting network, all in registers.  The thread
+//    first computes the face's area (FP64), which overlaps the gathers.
 __global__ void k_row_fill(const int2* __restrict__ face_tet, const int4* __restrict__ tface,
                            const int4* __restrict__ tmult, const int32_t* __restrict__ face_mult,
                            const int64_t* __restrict__ d_tot, int64_t nFmax,
                            const int32_t* __restrict__ rowptr, int32_t* __restrict__ colind,
                            int32_t* __restrict__ rowdiag, int32_t* __restrict__ tpos,
-                           unsigned short* __restrict__ trel, unsigned* status) {
+                           unsigned short* __restrict__ trel, const double* __restrict__ coord,
+                           const int32_t* __restrict__ face_vtx, double* __restrict__ area, unsigned* status) {
   const int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (F >= nFmax || F >= d_tot[0] || failed(status)) return;
+  face_area(coord, face_vtx, F, area);
   const int l = face_mult[F];
   if (l < 0) return;
   const int2 ft = face_tet[F];
@@ -516,40 +521,6 @@ __global__ void k_row_fill(const int2* __restrict__ face_tet, const int4* __rest
     tpos[4 * (int64_t)T[side] + k[side]] = base + rl;
     trel[4 * (int64_t)T[side] + k[side]] = (unsigned short)bits;
   }
-}
-
-// The FP64-bound parts of the build run on a second stream, beside the
-// integer and memory-bound connectivity kernels of the caller's stream, so
-// that the FP64 pipe and the others work at the same time: the element
-// geometry from the start, the face areas once k_face_emit has written the
-// face vertices.  Each is a grid of a few blocks per SM striding over its
-// range, so that it stays resident beside the other stream's kernels.
-constexpr int kSideThreads = 128;
-constexpr int kSideBlocksPerSM = 3;
-
-__global__ void __launch_bounds__(kSideThreads) k_tet_geometry(const int4* __restrict__ tet, int64_t nE, int64_t nC,
-                                                               const double* __restrict__ coord,
-                                                               double* __restrict__ geo, bool geo_dw,
-                                                               unsigned* status) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nE; i += stride) {
-    const int4 v = tet[i];
-    if (!valid_tet(v, nC)) continue;  // k_face_count reports it
-    if (geo_dw) tet_geom_dw(coord, v, i, geo, status);
-    else tet_geom(coord, v, i, geo, status);
-  }
-}
-
-// Ordered after k_face_emit: the status word then holds every connectivity
-// error, and face_vtx is valid when it is clear.
-__global__ void __launch_bounds__(kSideThreads) k_face_area(const double* __restrict__ coord,
-                                                            const int32_t* __restrict__ face_vtx,
-                                                            const int64_t* __restrict__ d_tot, int64_t nFmax,
-                                                            double* __restrict__ area, const unsigned* status) {
-  if (failed(status)) return;
-  const int64_t nF = min(nFmax, d_tot[0]), stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; F < nF; F += stride)
-    face_area(coord, face_vtx, F, area);
 }
 
 __global__ void k_face_centroid(const double* __restrict__ coord, const int32_t* __restrict__ face_vtx, int64_t nF,
@@ -625,68 +596,6 @@ struct BatchCounts {
   long long* h_counts;  // 3n (host)
 };
 
-namespace {
-
-// The build's second stream and its three events (fork, face vertices
-// written, join), one set per build in flight (builds from several host
-// threads do not share one), kept per device for reuse.  The stream has the
-// highest priority, so that the side kernels' blocks are placed first.
-struct SideStream {
-  cudaStream_t g = nullptr;
-  cudaEvent_t fork = nullptr, emitted = nullptr, join = nullptr;
-};
-std::mutex g_side_mu;
-std::vector<SideStream> g_side_free[64];
-int g_num_sms[64];
-
-cudaError_t acquire_side(int dev, SideStream* out) {
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  {
-    std::lock_guard<std::mutex> lk(g_side_mu);
-    if (!g_side_free[dev].empty()) {
-      *out = g_side_free[dev].back();
-      g_side_free[dev].pop_back();
-      return cudaSuccess;
-    }
-  }
-  SideStream x;
-  int lo = 0, hi = 0;
-  cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
-  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&x.g, cudaStreamNonBlocking, hi);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x.emitted, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming);
-  if (e != cudaSuccess) {
-    if (x.g) cudaStreamDestroy(x.g);
-    for (cudaEvent_t ev : {x.fork, x.emitted, x.join})
-      if (ev) cudaEventDestroy(ev);
-    return e;
-  }
-  *out = x;
-  return cudaSuccess;
-}
-
-void release_side(int dev, const SideStream& x) {
-  std::lock_guard<std::mutex> lk(g_side_mu);
-  g_side_free[dev].push_back(x);
-}
-
-// Grid of the side kernels: kSideBlocksPerSM blocks on every SM (fewer for
-// small ranges).
-cudaError_t side_grid(int dev, int64_t n, unsigned* grid) {
-  if (g_num_sms[dev] == 0) {
-    int v = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    g_num_sms[dev] = v;
-  }
-  const int64_t want = (n + kSideThreads - 1) / kSideThreads;
-  *grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)g_num_sms[dev] * kSideBlocksPerSM));
-  return cudaSuccess;
-}
-
-}  // namespace
-
 // Synchronise and read n device int64 counters and the status word.
 static ph_status read_counters(const int64_t* d_tot, int n, unsigned* d_status, cudaStream_t s, int64_t* tot,
                                unsigned* status) {
@@ -727,10 +636,7 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
   // synchronises once, at the end; int32 ids and CSR positions bound the size.
   const int64_t nFmax = 4 * nE + nN, nnzmax = nFmax + 12 * nE;
   if (nnzmax >= ((int64_t)1 << 31) - 1 || nC >= ((int64_t)1 << 31) - 1) return PH_ERR_OVERFLOW;
-  ph_status st = PH_OK;  // the connectivity in order on the caller's stream s, the geometry and areas beside it
-  SideStream side;
-  bool have_side = false, joined = false;
-  int dev = 0;
+  ph_status st = PH_OK;  // everything runs in order on the caller's stream s
   // face-key buckets: 4 per largest vertex while the bucket ids stay below 2^31
   // (finer buckets shorten the match scans but cost more in the scattered
   // fill and the bucket scan than they save)
@@ -766,7 +672,6 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
   const size_t o_rowlen2 = sc.take<int32_t>(nN > 0 || nE == 0 ? 0 : nFmax + 1);
   void* scratch = nullptr;
   PH_CU(cudaGetDevice(&m->device), "cudaGetDevice");
-  dev = m->device;
   m->nE = nE;
   m->nC = nC;
   PH_CU(alloc_bytes(&m->arena, mc.bytes, s), "alloc mesh");
@@ -806,18 +711,6 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
   PH_CU(cudaMemsetAsync(scratch, 0, zero_bytes, s), "memset");
   PH_CU(cudaMemsetAsync(m->status, 0, sizeof(unsigned), s), "memset");
   if (nC > 0) PH_CU(cudaMemcpyAsync(m->coord, coord, sizeof(double) * 3 * nC, cudaMemcpyDeviceToDevice, s), "copy");
-  if (nE > 0) {  // fork: the element geometry on the second stream, from the caller's tets
-    unsigned g = 0;
-    PH_CU(acquire_side(dev, &side), "mesh_create side stream");
-    have_side = true;
-    PH_CU(side_grid(dev, nE, &g), "cudaDeviceGetAttribute");
-    PH_CU(cudaEventRecord(side.fork, s), "cudaEventRecord");
-    PH_CU(cudaStreamWaitEvent(side.g, side.fork, 0), "cudaStreamWaitEvent");
-    KernelTimer kt("k_tet_geometry", side.g, 2);
-    k_tet_geometry<<<g, kSideThreads, 0, side.g>>>(reinterpret_cast<const int4*>(tet), nE, nC, m->coord, m->geo, dw,
-                                                   m->status);
-    PH_CU(launched(), "k_tet_geometry");
-  }
 
   // --- faces: bucket the keys, match them, number the faces ----------------
   if (nent > 0) {
@@ -831,7 +724,7 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
     {
       KernelTimer kt("k_face_fill", s, 2);
       k_face_fill<<<grid_for(nE + nN), kThreads, 0, s>>>(m->tet, nE, nC, neumann, nN, sub, start, cnt, entries,
-                                                         mate, m->status);
+                                                         mate, m->coord, m->geo, dw, m->status);
       PH_CU(launched(), "k_face_fill");
     }
     {
@@ -849,15 +742,6 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
         m->tet, nE, reinterpret_cast<int4*>(mate), newc, m->tface, m->face_tet, m->face_vtx, m->face_kind, flag,
         nN > 0 ? nullptr : m->face_mult, m->tmult, rowlen, m->status);
     PH_CU(launched(), "k_face_emit");
-  }
-  if (have_side) {  // the face areas on the second stream, once the face vertices are written
-    unsigned g = 0;
-    PH_CU(side_grid(dev, nFmax, &g), "cudaDeviceGetAttribute");
-    PH_CU(cudaEventRecord(side.emitted, s), "cudaEventRecord");
-    PH_CU(cudaStreamWaitEvent(side.g, side.emitted, 0), "cudaStreamWaitEvent");
-    KernelTimer kt("k_face_area", side.g, 2);
-    k_face_area<<<g, kSideThreads, 0, side.g>>>(m->coord, m->face_vtx, d_tot, nFmax, m->face_area, m->status);
-    PH_CU(launched(), "k_face_area");
   }
 
   // --- multipliers and CSR pattern (rows sized by nFmax >= L) ---------------
@@ -880,7 +764,8 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
     KernelTimer kt("k_row_fill", s, 2);
     k_row_fill<<<gF, kThreads, 0, s>>>(m->face_tet, m->tface, m->tmult, m->face_mult, d_tot, nFmax, m->rowptr,
                                        m->colind, m->rowdiag, reinterpret_cast<int32_t*>(m->tpos),
-                                       reinterpret_cast<unsigned short*>(m->trel), m->status);
+                                       reinterpret_cast<unsigned short*>(m->trel), m->coord, m->face_vtx,
+                                       m->face_area, m->status);
     PH_CU(launched(), "k_row_fill");
   }
   if (bc && bc->n > 0) {  // per-problem offsets of a batched build
@@ -890,16 +775,9 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
     PH_CU(cudaMemcpyAsync(bc->h_counts, bc->d_counts, sizeof(long long) * 3 * bc->n, cudaMemcpyDeviceToHost, s),
           "copy");
   }
-  if (have_side) {  // join
-    joined = true;
-    PH_CU(cudaEventRecord(side.join, side.g), "cudaEventRecord");
-    PH_CU(cudaStreamWaitEvent(s, side.join, 0), "cudaStreamWaitEvent");
-  }
   // the one synchronisation: counts and the first error of any kernel
   PH_TRY(read_counters(d_tot, 3, m->status, s, tot, &bits));
   }
-  if (have_side) release_side(dev, side);
-  have_side = false;
   free_async(scratch, s);
   scratch = nullptr;
   if (bits) { st = status_from_bits(bits); goto fail; }
@@ -916,11 +794,6 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
   return PH_OK;
 
 fail:
-  if (have_side) {  // the frees below are ordered after the second stream's work
-    if (!joined && cudaEventRecord(side.join, side.g) == cudaSuccess) cudaStreamWaitEvent(s, side.join, 0);
-    cudaStreamSynchronize(side.g);
-    release_side(dev, side);
-  }
   free_async(scratch, s);
   mesh_free(m, s);
   return st;
