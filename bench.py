@@ -729,7 +729,7 @@ def adjoint_section(ph, dev, rtol=1e-10):
         return J, grad, [it1, it2], [ev[i].elapsed_time(ev[i + 1]) for i in range(7)]
 
     J, grad, its, t = gradient("f64")
-    J32, grad32, its32, t32 = gradient("dw")
+    J32, grad32, its32, t32 = gradient("f32")
     total = sum(t)
     adj_kernels_ms = t[4] + t[6]
     it1, it2 = its
@@ -742,9 +742,9 @@ def adjoint_section(ph, dev, rtol=1e-10):
         "pcg_iterations": [it1, it2], "pcg_rtol": rtol, "preconditioner": "edge-patch additive Schwarz",
         "adjoint_kernels_tets_per_s": p.nE / (adj_kernels_ms * 1e-3),
         "note": "gradient time is dominated by the two PCG solves of the condensed system",
-        "double_word_patch_blocks": {
-            "what": "the same gradient with ph_schwarz_create_dw: patch inverses stored as float pairs and applied "
-                    "in double-word arithmetic on the FP32 pipe; residual, updates and stopping test in fp64",
+        "fp32_patch_blocks": {
+            "what": "the same gradient with ph_schwarz_create_f32: patch inverses stored and applied in fp32, "
+                    "residual, updates and stopping test in fp64",
             "ms_per_gradient": sum(t32), "grads_per_s": 1000.0 / sum(t32), "speedup": total / sum(t32),
             "pcg_iterations": its32,
             "ms": {"schwarz_setup": t32[1], "forward_solve": t32[2], "adjoint_solve": t32[5]},
@@ -825,7 +825,7 @@ def cpu_baseline(p, workload, budget_s=15.0):
 def profile_pcg(iters, precision="f64"):
     """A fixed number of Schwarz-preconditioned PCG iterations on the adjoint
     workload's system (Kuhn 6^3 cube, 3 levels, c = 0.1, lognormal a with
-    seed 51), with fp64 or double-word patch blocks: a target for profiler launch
+    seed 51), with fp64 or fp32 patch blocks: a target for profiler launch
     lists of the solve."""
     import torch
     import paper_2509_11133_gb300 as ph
@@ -966,7 +966,7 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=3.0)
     ap.add_argument("--profile-pcg", type=int, default=0, metavar="N",
                     help="profiler target: N Schwarz-PCG iterations on the adjoint workload, then exit")
-    ap.add_argument("--pcg-precision", default="f64", choices=["f64", "dw"],
+    ap.add_argument("--pcg-precision", default="f64", choices=["f64", "f32"],
                     help="Schwarz patch blocks used by --profile-pcg")
     ap.add_argument("--profile-kernels", type=int, default=0, metavar="R",
                     help="profiler target: R rounds of the element kernels (assembly, recovery, misfit, adjoint) "

@@ -5,10 +5,6 @@
 
 #include "ph_internal.cuh"
 
-namespace dw {
-struct f2;
-}
-
 namespace ph_pcg {
 
 constexpr int RT = 256;   // threads per block
@@ -60,11 +56,11 @@ __device__ __forceinline__ bool last_block(unsigned* done) {
 
 // z = M r for the edge-patch Schwarz preconditioner P (y: scratch of
 // P->nmem doubles), with the sum r.z: init sets rz, otherwise the last block
-// sets beta = r.z / rz_old and rz.  Two launches.  With double-word blocks
-// the patch solves take r scaled by a power of two near 1/sqrt(r.r) (sc->rr,
-// set before).
-cudaError_t schwarz_apply(const ph_schwarz* P, const double* r, double* z, double* y, double* part, Scalars* sc,
-                          bool init, cudaStream_t s);
+// sets beta and rz.  Two launches.  With fp32 blocks the patch solves run in
+// fp32 on r scaled by a power of two near 1/sqrt(r.r) (sc->rr, set before),
+// and beta is the flexible one, -alpha z.q / rz_old (q = H p, unused at init).
+cudaError_t schwarz_apply(const ph_schwarz* P, const double* r, const double* q, double* z, double* y, double* part,
+                          Scalars* sc, bool init, cudaStream_t s);
 
 }  // namespace ph_pcg
 
@@ -90,7 +86,6 @@ struct ph_schwarz {
   SchwarzGroups g;
   int32_t* mem;    // multiplier ids, ascending within a patch
   double* blk;     // patch inverses: packed upper triangle, row-major (fp64), or null
-  dw::f2* blkdw;   // the same as float pairs times 2^-bexp (ph_schwarz_create_dw), or null
-  int32_t* bexp;   // per patch (patch order): the binade of its largest inverse entry
+  float* blk32;    // the same rounded to fp32 (ph_schwarz_create_f32), or null
   int32_t* fslot;  // 3L: positions in mem (and y) of each multiplier in the patches of its face's three edges
 };

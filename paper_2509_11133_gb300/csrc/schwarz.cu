@@ -15,19 +15,16 @@
 // (sums in member order) with the block in registers, then one thread per
 // multiplier adds the three values of its face's three edges in a fixed order
 // -- no atomics, so a solve repeats bit for bit.
-// Double-word blocks (ph_schwarz_create_dw): the blocks are factored and
-// inverted in fp64 as above and stored as float pairs (dw.cuh) scaled by a
-// power of two per patch, and the patch solves run in double-word arithmetic
-// on the FP32 pipe (the fp64 ones are FP64-bound: K^2 FMA per patch); each
-// patch value goes back to fp64 exactly scaled, and everything after is the
-// fp64 path.  The pairs carry ~48 bits, so the preconditioner is the fp64
-// one to ~1e-14 and the iteration counts match.  (Blocks rounded to plain
-// fp32 lose the near-null directions of the ill-conditioned patch blocks:
-// 4.6x the iterations on the 1e4-contrast checkerboard.)
+// Mixed precision (ph_schwarz_create_f32): the blocks are factored and
+// inverted in fp64 as above and stored rounded to fp32, and the patch solves
+// run on the FP32 pipe (the fp64 ones are FP64-bound: K^2 FMA per patch).  A
+// preconditioner only steers the iteration -- the residual, the updates and
+// the stopping test stay fp64 -- so the solution's accuracy is unchanged;
+// the rounding of M (~1e-7 relative, symmetric storage) changes the
+// iteration count slightly.
 #include <math.h>
 #include <string.h>
 
-#include "dw.cuh"
 #include "edges.cuh"
 #include "pcg.cuh"
 #include "ph_internal.cuh"
@@ -163,19 +160,19 @@ __device__ __forceinline__ int group_of(const SchwarzGroups& g, int64_t t) {
 }
 
 // Invert each patch block: Cholesky A = G G', then A^-1 = G^-T G^-1 (upper
-// triangle stored, slot-major within the group): fp64 into blk, or (DW) as
-// float pairs into blkdw scaled by 2^-bexp[t], bexp[t] the binade of the
-// patch's largest entry.
-template <bool DW>
+// triangle stored, slot-major within the group).
+// T = float: the inverse rounded to fp32, PH_ERR_ARG for an entry outside
+// [2^-100, 2^100] in magnitude (fp32 range with room for the products).
+template <typename T>
 __global__ void k_group_factor(SchwarzGroups g, int64_t npatch, const int32_t* __restrict__ mem,
                                const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                               const double* __restrict__ values, double* __restrict__ blk,
-                               dw::f2* __restrict__ blkdw, int32_t* __restrict__ bexp, unsigned* status) {
+                               const double* __restrict__ values, T* __restrict__ blk, unsigned* status) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= npatch) return;
   const int k = group_of(g, t);
   const int64_t s = t - g.first[k], n = g.count[k];
   const int32_t* mm = mem + g.mbase[k] + s;  // member i at mm[i n]
+  T* out = blk + g.bbase[k] + s;             // entry q at out[q n]
   constexpr int K = kSchwarzDense;
   double a[K * K];  // lower Cholesky factor, then its inverse (row-major)
   for (int i = 0; i < k; ++i)
@@ -204,31 +201,14 @@ __global__ void k_group_factor(SchwarzGroups g, int64_t npatch, const int32_t* _
       a[i * K + j] = v / a[i * K + i];
     }
   }
-  // A^-1 = G^-T G^-1: (i, j) = sum_{q >= max(i, j)} Gi[q][i] Gi[q][j]; with
-  // DW, a first pass finds the largest entry's binade
-  int ep = 0;
-  if (DW) {
-    double mx = 0.0;
-    for (int i = 0; i < k; ++i)
-      for (int j = i; j < k; ++j) {
-        double v = 0.0;
-        for (int q = j; q < k; ++q) v += a[q * K + i] * a[q * K + j];
-        mx = fmax(mx, fabs(v));
-      }
-    if (!(mx > 0.0 && mx < 1e300)) {
-      ph_flag(status, PH_ERR_ARG);
-      return;
-    }
-    ep = dw::exponent(mx);
-    bexp[t] = ep;
-  }
+  // A^-1 = G^-T G^-1: (i, j) = sum_{q >= max(i, j)} Gi[q][i] Gi[q][j]
   for (int i = 0; i < k; ++i)
     for (int j = i; j < k; ++j) {
       double v = 0.0;
       for (int q = j; q < k; ++q) v += a[q * K + i] * a[q * K + j];
-      const int64_t at = g.bbase[k] + s + (int64_t)upper(i, j, k) * n;
-      if (DW) blkdw[at] = dw::from_double(v, -ep);
-      else blk[at] = v;
+      if (sizeof(T) == sizeof(float) && v != 0.0 && !(fabs(v) >= 0x1p-100 && fabs(v) <= 0x1p100))
+        ph_flag(status, PH_ERR_ARG);
+      out[(int64_t)upper(i, j, k) * n] = (T)v;
     }
 }
 
@@ -247,111 +227,87 @@ __device__ __forceinline__ int residual_shift(double rr) {
   return -((e >> 1) + 1);
 }
 
+// x 2^k rounded to nearest fp32 with integer instructions (on this part the
+// F2F conversions issue on the FP64 pipe, at its rate); results below 2^-126
+// flush to zero.  |x| 2^k < 2^127.
+__device__ __forceinline__ float to_f32(double x, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int f = (int)((b >> 52) & 0x7FF);
+  const int e = f - 1023 + k;
+  if (f == 0 || e < -126) return __uint_as_float(sign);
+  const unsigned m = (unsigned)(b >> 29) & 0x7FFFFFu;  // the top 23 fraction bits
+  const unsigned rest = (unsigned)b & 0x1FFFFFFFu;     // the other 29
+  const unsigned up = rest > 0x10000000u || (rest == 0x10000000u && (m & 1u));  // to nearest even
+  return __uint_as_float(sign | ((((unsigned)(e + 127) << 23) | m) + up));
+}
+
+// x 2^k as fp64 with integer instructions (exact; x finite, the result normal).
+__device__ __forceinline__ double to_f64(float x, int k) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned f = (b >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  if (f == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long ex = (unsigned long long)((int)f - 127 + k + 1023);
+  return __longlong_as_double((long long)(sign | (ex << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
+__device__ __forceinline__ float mad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+__device__ __forceinline__ double load_r(const double* r, int64_t i, int, double) { return __ldg(r + i); }
+__device__ __forceinline__ float load_r(const double* r, int64_t i, int k, float) { return to_f32(__ldg(r + i), k); }
+
 // y = block^-1 r_patch for one patch of K members (slot-major group arrays,
-// stride n): the packed inverse in registers, sums in member order.
-template <int K>
+// stride n): the packed inverse in registers, sums in member order.  T: the
+// blocks' and y's type; for float, r enters scaled by 2^k.
+template <int K, typename T>
 __device__ __forceinline__ void patch_solve(int64_t s, int64_t n, const int32_t* __restrict__ mem,
-                                            const double* __restrict__ blk, const double* __restrict__ r,
-                                            double* __restrict__ y) {
+                                            const T* __restrict__ blk, const double* __restrict__ r, int k,
+                                            T* __restrict__ y) {
   constexpr int NQ = K * (K + 1) / 2;
-  double m[NQ], rv[K];
+  T m[NQ], rv[K];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) m[q] = __ldcs(blk + q * n + s);
 #pragma unroll
-  for (int j = 0; j < K; ++j) rv[j] = __ldg(r + __ldg(mem + j * n + s));
+  for (int j = 0; j < K; ++j) rv[j] = load_r(r, __ldg(mem + j * n + s), k, T());
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    double v = 0.0;
+    T v = 0;
 #pragma unroll
-    for (int j = 0; j < K; ++j) v = fma(m[i <= j ? upper(i, j, K) : upper(j, i, K)], rv[j], v);
+    for (int j = 0; j < K; ++j) v = mad(m[i <= j ? upper(i, j, K) : upper(j, i, K)], rv[j], v);
     y[i * n + s] = v;
   }
 }
 
-// The same in double-word arithmetic: r scaled by 2^sh as pairs (integer
-// conversions), each stored pair of the scaled inverse read once and applied
-// to both of its rows (products and sums in double-word; every row still
-// sums its terms in member order), each value back to fp64 times 2^(ep - sh)
-// (exact).
-template <int K>
-__device__ __forceinline__ void patch_solve_dw(int64_t s, int64_t n, const int32_t* __restrict__ mem,
-                                               const dw::f2* __restrict__ blk, int ep, int sh,
-                                               const double* __restrict__ r, double* __restrict__ y) {
-  dw::f2 rv[K], v[K];
-  const float2* b2 = reinterpret_cast<const float2*>(blk);
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    rv[j] = dw::from_double(__ldg(r + __ldg(mem + j * n + s)), sh);
-    v[j] = dw::f2{0.f, 0.f};
-  }
-#pragma unroll
-  for (int i = 0; i < K; ++i)
-#pragma unroll
-    for (int j = i; j < K; ++j) {
-      const float2 x = __ldcs(b2 + upper(i, j, K) * n + s);
-      const dw::f2 m{x.x, x.y};
-      v[i] = dw::add(v[i], dw::mul(m, rv[j]));
-      if (j != i) v[j] = dw::add(v[j], dw::mul(m, rv[i]));
-    }
-#pragma unroll
-  for (int i = 0; i < K; ++i) y[i * n + s] = dw::to_double(v[i], ep - sh);
-}
-
-template <bool DW>
+template <typename T>
 __global__ void __launch_bounds__(256) k_schwarz_patch(SchwarzGroups g, int64_t npatch,
-                                                       const int32_t* __restrict__ mem,
-                                                       const double* __restrict__ blk,
-                                                       const dw::f2* __restrict__ blkdw,
-                                                       const int32_t* __restrict__ bexp,
+                                                       const int32_t* __restrict__ mem, const T* __restrict__ blk,
                                                        const double* __restrict__ r, const Scalars* __restrict__ sc,
-                                                       double* __restrict__ y) {
+                                                       T* __restrict__ y) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= npatch) return;
+  const int sh = sizeof(T) == sizeof(float) ? residual_shift(sc->rr) : 0;
   const int k = group_of(g, t);
   const int64_t s = t - g.first[k], n = g.count[k];
   const int32_t* mm = mem + g.mbase[k];
-  double* yy = y + g.mbase[k];
-  if (DW) {
-    const int sh = residual_shift(sc->rr), ep = __ldg(bexp + t);
-    const dw::f2* bb = blkdw + g.bbase[k];
-    switch (k) {
-      case 1: patch_solve_dw<1>(s, n, mm, bb, ep, sh, r, yy); return;
-      case 2: patch_solve_dw<2>(s, n, mm, bb, ep, sh, r, yy); return;
-      case 3: patch_solve_dw<3>(s, n, mm, bb, ep, sh, r, yy); return;
-      case 4: patch_solve_dw<4>(s, n, mm, bb, ep, sh, r, yy); return;
-      case 5: patch_solve_dw<5>(s, n, mm, bb, ep, sh, r, yy); return;
-      case 6: patch_solve_dw<6>(s, n, mm, bb, ep, sh, r, yy); return;
-      case 7: patch_solve_dw<7>(s, n, mm, bb, ep, sh, r, yy); return;
-      case 8: patch_solve_dw<8>(s, n, mm, bb, ep, sh, r, yy); return;
-      default: {  // 9..kSchwarzDense members: rare; the block read entry by entry
-        dw::f2 rv[kSchwarzDense];
-        for (int j = 0; j < k; ++j) rv[j] = dw::from_double(__ldg(r + __ldg(mm + j * n + s)), sh);
-        for (int i = 0; i < k; ++i) {
-          dw::f2 v{0.f, 0.f};
-          for (int j = 0; j < k; ++j) v = dw::add(v, dw::mul(bb[(int64_t)(i <= j ? upper(i, j, k) : upper(j, i, k)) * n + s],
-                                                             rv[j]));
-          yy[i * n + s] = dw::to_double(v, ep - sh);
-        }
-        return;
-      }
-    }
-  }
-  const double* bb = blk + g.bbase[k];
+  const T* bb = blk + g.bbase[k];
+  T* yy = y + g.mbase[k];
   switch (k) {  // uniform across a warp except at the group boundaries
-    case 1: patch_solve<1>(s, n, mm, bb, r, yy); break;
-    case 2: patch_solve<2>(s, n, mm, bb, r, yy); break;
-    case 3: patch_solve<3>(s, n, mm, bb, r, yy); break;
-    case 4: patch_solve<4>(s, n, mm, bb, r, yy); break;
-    case 5: patch_solve<5>(s, n, mm, bb, r, yy); break;
-    case 6: patch_solve<6>(s, n, mm, bb, r, yy); break;
-    case 7: patch_solve<7>(s, n, mm, bb, r, yy); break;
-    case 8: patch_solve<8>(s, n, mm, bb, r, yy); break;
+    case 1: patch_solve<1>(s, n, mm, bb, r, sh, yy); break;
+    case 2: patch_solve<2>(s, n, mm, bb, r, sh, yy); break;
+    case 3: patch_solve<3>(s, n, mm, bb, r, sh, yy); break;
+    case 4: patch_solve<4>(s, n, mm, bb, r, sh, yy); break;
+    case 5: patch_solve<5>(s, n, mm, bb, r, sh, yy); break;
+    case 6: patch_solve<6>(s, n, mm, bb, r, sh, yy); break;
+    case 7: patch_solve<7>(s, n, mm, bb, r, sh, yy); break;
+    case 8: patch_solve<8>(s, n, mm, bb, r, sh, yy); break;
     default: {  // 9..kSchwarzDense members: rare; the block read entry by entry
-      double rv[kSchwarzDense];
-      for (int j = 0; j < k; ++j) rv[j] = __ldg(r + __ldg(mm + j * n + s));
+      T rv[kSchwarzDense];
+      for (int j = 0; j < k; ++j) rv[j] = load_r(r, __ldg(mm + j * n + s), sh, T());
       for (int i = 0; i < k; ++i) {
-        double v = 0.0;
-        for (int j = 0; j < k; ++j) v = fma(__ldg(bb + (int64_t)(i <= j ? upper(i, j, k) : upper(j, i, k)) * n + s),
+        T v = 0;
+        for (int j = 0; j < k; ++j) v = mad(__ldg(bb + (int64_t)(i <= j ? upper(i, j, k) : upper(j, i, k)) * n + s),
                                             rv[j], v);
         yy[i * n + s] = v;
       }
@@ -360,28 +316,44 @@ __global__ void __launch_bounds__(256) k_schwarz_patch(SchwarzGroups g, int64_t 
 }
 
 // z = sum of the three patch values of each multiplier (fixed order), r.z;
-// the last block sets rz (init) or beta = r.z / rz_old and rz.
+// the last block sets rz (init) or beta and rz.  fp64 blocks: beta = r.z /
+// rz_old.  fp32 blocks (y scaled by 2^sh, summed in fp32): the flexible
+// (Polak-Ribiere) beta = z.(r - r_old) / rz_old = -alpha z.q / rz_old, which
+// keeps conjugate gradients converging when the preconditioner's rounding
+// varies with r; z.q is summed beside r.z (q = H p of this iteration).
+template <typename T>
 __global__ void __launch_bounds__(RT) k_schwarz_face(int64_t L, const int32_t* __restrict__ fslot,
-                                                     const double* __restrict__ y, const double* __restrict__ r,
-                                                     double* __restrict__ z, double* __restrict__ part,
-                                                     Scalars* __restrict__ sc, bool init) {
-  double rz = 0.0;
+                                                     const T* __restrict__ y, const double* __restrict__ r,
+                                                     const double* __restrict__ q, double* __restrict__ z,
+                                                     double* __restrict__ part, Scalars* __restrict__ sc, bool init) {
+  constexpr bool F32 = sizeof(T) == sizeof(float);
+  const int sh = F32 ? residual_shift(sc->rr) : 0;
+  double rz = 0.0, zq = 0.0;
   for (int64_t l = blockIdx.x * (int64_t)RT + threadIdx.x; l < L; l += (int64_t)RB * RT) {
     const int s0 = fslot[3 * l], s1 = fslot[3 * l + 1], s2 = fslot[3 * l + 2];
-    const double zl = (y[s0] + y[s1]) + y[s2];
+    double zl;
+    if (F32) zl = to_f64((float)((y[s0] + y[s1]) + y[s2]), -sh);
+    else zl = ((double)y[s0] + (double)y[s1]) + (double)y[s2];
     z[l] = zl;
     rz = fma(r[l], zl, rz);
+    if (F32 && !init) zq = fma(q[l], zl, zq);
   }
   rz = block_sum(rz);
   if (threadIdx.x == 0) part[RB + blockIdx.x] = rz;
+  if (F32 && !init) {
+    zq = block_sum(zq);
+    if (threadIdx.x == 0) part[blockIdx.x] = zq;  // p.q's partials were consumed by alpha
+  }
   if (last_block(&sc->done)) {
     const double rz_t = sum_partials(part, RB);
+    const double zq_t = F32 && !init ? sum_partials(part, 0) : 0.0;
     if (threadIdx.x == 0) {
       if (init) {
         sc->beta = 0.0;
       } else {
         const double rz_old = sc->rz;
-        sc->beta = rz_old > 0.0 ? rz_t / rz_old : 0.0;
+        const double num = F32 ? -sc->alpha * zq_t : rz_t;
+        sc->beta = rz_old > 0.0 ? num / rz_old : 0.0;
       }
       sc->rz = rz_t;
       sc->done = 0;
@@ -393,17 +365,18 @@ __global__ void __launch_bounds__(RT) k_schwarz_face(int64_t L, const int32_t* _
 
 namespace ph_pcg {
 
-cudaError_t schwarz_apply(const ph_schwarz* P, const double* r, double* z, double* y, double* part, Scalars* sc,
-                          bool init, cudaStream_t s) {
-  if (P->npatch > 0) {
-    if (P->blkdw)
-      k_schwarz_patch<true><<<ph::grid_for(P->npatch), 256, 0, s>>>(P->g, P->npatch, P->mem, nullptr, P->blkdw,
-                                                                    P->bexp, r, sc, y);
-    else
-      k_schwarz_patch<false><<<ph::grid_for(P->npatch), 256, 0, s>>>(P->g, P->npatch, P->mem, P->blk, nullptr,
-                                                                     nullptr, r, sc, y);
+cudaError_t schwarz_apply(const ph_schwarz* P, const double* r, const double* q, double* z, double* y, double* part,
+                          Scalars* sc, bool init, cudaStream_t s) {
+  if (P->blk32) {  // fp32 patch values in the first half of y's scratch
+    float* y32 = reinterpret_cast<float*>(y);
+    if (P->npatch > 0)
+      k_schwarz_patch<float><<<ph::grid_for(P->npatch), 256, 0, s>>>(P->g, P->npatch, P->mem, P->blk32, r, sc, y32);
+    k_schwarz_face<float><<<RB, RT, 0, s>>>(P->L, P->fslot, y32, r, q, z, part, sc, init);
+  } else {
+    if (P->npatch > 0)
+      k_schwarz_patch<double><<<ph::grid_for(P->npatch), 256, 0, s>>>(P->g, P->npatch, P->mem, P->blk, r, sc, y);
+    k_schwarz_face<double><<<RB, RT, 0, s>>>(P->L, P->fslot, y, r, q, z, part, sc, init);
   }
-  k_schwarz_face<<<RB, RT, 0, s>>>(P->L, P->fslot, y, r, z, part, sc, init);
   return ph::launched(P->npatch > 0 ? 2 : 1);
 }
 
@@ -415,25 +388,24 @@ static void schwarz_free(ph_schwarz* P, cudaStream_t s) {
   if (!P) return;
   free_async(P->mem, s);
   free_async(P->blk, s);
-  free_async(P->blkdw, s);
-  free_async(P->bexp, s);
+  free_async(P->blk32, s);
   free_async(P->fslot, s);
   delete P;
 }
 
-static ph_status schwarz_create(const ph_mesh* m, const double* values, cudaStream_t s, bool dw,
+static ph_status schwarz_create(const ph_mesh* m, const double* values, cudaStream_t s, bool f32,
                                 ph_schwarz** out);
 
 extern "C" ph_status ph_schwarz_create(const ph_mesh* m, const double* values, void* stream, ph_schwarz** out) {
   return schwarz_create(m, values, (cudaStream_t)stream, false, out);
 }
 
-extern "C" ph_status ph_schwarz_create_dw(const ph_mesh* m, const double* values, void* stream,
-                                          ph_schwarz** out) {
+extern "C" ph_status ph_schwarz_create_f32(const ph_mesh* m, const double* values, void* stream,
+                                           ph_schwarz** out) {
   return schwarz_create(m, values, (cudaStream_t)stream, true, out);
 }
 
-static ph_status schwarz_create(const ph_mesh* m, const double* values, cudaStream_t s, bool dw,
+static ph_status schwarz_create(const ph_mesh* m, const double* values, cudaStream_t s, bool f32,
                                 ph_schwarz** out) {
   if (!out) return PH_ERR_ARG;
   *out = nullptr;
@@ -516,9 +488,7 @@ static ph_status schwarz_create(const ph_mesh* m, const double* values, cudaStre
 
   // placement (one deterministic pass per occupied group) and face slots
   e = alloc(&P->mem, (size_t)P->nmem, s);
-  if (e == cudaSuccess && dw) e = alloc(&P->blkdw, (size_t)P->nblk, s);
-  if (e == cudaSuccess && dw) e = alloc(&P->bexp, (size_t)P->npatch, s);
-  if (e == cudaSuccess && !dw) e = alloc(&P->blk, (size_t)P->nblk, s);
+  if (e == cudaSuccess) e = f32 ? alloc(&P->blk32, (size_t)P->nblk, s) : alloc(&P->blk, (size_t)P->nblk, s);
   if (e == cudaSuccess) e = alloc(&m2f, (size_t)L, s);
   if (e == cudaSuccess) e = alloc(&P->fslot, (size_t)(3 * L), s);
   if (e == cudaSuccess) e = alloc(&ind, (size_t)P->nEd + 1, s);
@@ -543,18 +513,23 @@ static ph_status schwarz_create(const ph_mesh* m, const double* values, cudaStre
     if (e != cudaSuccess) { st = cuda_status(e, "ph_schwarz_create"); goto done; }
   }
   if (P->npatch > 0) {
-    if (dw)
-      k_group_factor<true><<<grid_for(P->npatch, 128), 128, 0, s>>>(g, P->npatch, P->mem, m->rowptr, m->colind,
-                                                                    values, nullptr, P->blkdw, P->bexp, status);
+    if (f32)
+      k_group_factor<float><<<grid_for(P->npatch, 128), 128, 0, s>>>(g, P->npatch, P->mem, m->rowptr, m->colind,
+                                                                     values, P->blk32, status);
     else
-      k_group_factor<false><<<grid_for(P->npatch, 128), 128, 0, s>>>(g, P->npatch, P->mem, m->rowptr, m->colind,
-                                                                     values, P->blk, nullptr, nullptr, status);
+      k_group_factor<double><<<grid_for(P->npatch, 128), 128, 0, s>>>(g, P->npatch, P->mem, m->rowptr, m->colind,
+                                                                      values, P->blk, status);
     e = launched();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { st = cuda_status(e, "ph_schwarz_create"); goto done; }
-  if (bits) st = status_from_bits(bits);
+  if (bits) {
+    st = status_from_bits(bits);
+    if (f32 && st == PH_ERR_ARG)
+      set_error_text("ph_schwarz_create_f32: a patch block is not positive definite, or its inverse is outside "
+                     "the fp32 range (ph_schwarz_create keeps it in fp64)");
+  }
 
 done:
   release_edges(E, s);

@@ -135,68 +135,64 @@ def test_schwarz_solve_repeatable(ph):
 
 
 # ---------------------------------------------------------------------------
-# double-word patch blocks (ph_schwarz_create_dw)
+# fp32 patch blocks (ph_schwarz_create_f32)
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("name", CASES)
-def test_double_word_blocks_same_solve(ph, name):
-    """With double-word patch blocks the solve reaches the same bar against
-    the oracle's exact solution, in the fp64 blocks' iteration count give or
-    take one check interval (8), also on the 1e4-contrast checkerboard whose
-    ill-conditioned patch blocks defeat plain fp32 blocks (both printed)."""
+def test_fp32_blocks_same_accuracy(ph, name):
+    """The solve with fp32 patch blocks reaches the same bar against the
+    oracle's exact solution (the residual and the stopping test are fp64),
+    in at most 10% more iterations than with the fp64 blocks (both printed)."""
     p = make(name)
     m, values, rhs, rowptr, colind, host_sys = system(ph, p)
     P64 = ph.Schwarz(m, values)
-    Pdw = ph.Schwarz(m, values, precision="dw")
+    P32 = ph.Schwarz(m, values, precision="f32")
     x64, it64, _, _ = P64.solve(values, rhs, rtol=1e-12, maxit=20000)
-    xdw, itdw, rrdw, _ = Pdw.solve(values, rhs, rtol=1e-12, maxit=20000)
+    x32, it32, rr32, _ = P32.solve(values, rhs, rtol=1e-12, maxit=20000)
     rp, ci, va, b = host_sys
     ref, _, _ = oracle.solve_refined(rp, ci, va, b)
     H = sp.csr_matrix((va, ci, rp), shape=(m.L, m.L))
-    x = xdw.cpu().numpy()
+    x = x32.cpu().numpy()
     err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
     err64 = np.linalg.norm(x64.cpu().numpy() - ref) / np.linalg.norm(ref)
-    print(f"{name}: double-word blocks {itdw} iterations, error {err:.3e}; fp64 blocks {it64} iterations, "
+    print(f"{name}: fp32 blocks {it32} iterations, error {err:.3e}; fp64 blocks {it64} iterations, "
           f"error {err64:.3e}")
-    assert rrdw <= 1e-12
+    assert rr32 <= 1e-12
     assert np.linalg.norm(b - H @ x) <= 1e-11 * np.linalg.norm(b)
     assert err <= SOLVE_RTOL
-    assert abs(itdw - it64) <= 8
+    assert it32 <= 1.1 * it64 + 8
     P64.close()
-    Pdw.close()
+    P32.close()
     m.close()
 
 
-def test_double_word_blocks_repeatable_and_refined(ph):
+def test_fp32_blocks_repeatable_and_refined(ph):
     p = make("jitter_checker_m1_k3")
     m, values, rhs, _, _, host_sys = system(ph, p)
-    P = ph.Schwarz(m, values, precision="dw")
+    P = ph.Schwarz(m, values, precision="f32")
     x1, it1, _, _ = P.solve(values, rhs, rtol=1e-11)
     x2, it2, _, _ = P.solve(values, rhs, rtol=1e-11)
     assert it1 == it2 and torch.equal(x1, x2)
     x, steps, it, corr, _ = ph.solve_refined(m, values, rhs, P, tol=1e-15, inner_rtol=1e-8, maxit=200000)
     ref, _, _ = oracle.solve_refined(*host_sys)
     err = np.linalg.norm(x.cpu().numpy() - ref) / np.linalg.norm(ref)
-    print(f"refined with double-word blocks: {steps} steps, {it} iterations, error {err:.2e}")
+    print(f"refined with fp32 blocks: {steps} steps, {it} iterations, error {err:.2e}")
     assert corr <= 1e-15 and err <= 1e-12
     P.close()
     m.close()
 
 
-@pytest.mark.parametrize("scale", [1e-40, 1e40])
-def test_double_word_blocks_any_scale(ph, scale):
-    """a and c scaled together by 1e-40 or 1e40 scale H and rhs by 1e40 or
-    1e-40 and the patch inverses the other way, beyond the float range: the
-    per-patch power of two keeps the pairs in range, and Lambda (the fluxes,
-    which do not change) comes out in the fp64 blocks' iterations."""
+def test_fp32_blocks_out_of_range(ph):
+    """c = 1e-32 makes H ~ 1/c and the patch inverses ~1e-32, below the fp32
+    blocks' range: ph_schwarz_create_f32 refuses with PH_ERR_ARG and says so;
+    the fp64 blocks still solve."""
     p = make("sin_kuhn")
     m = ph.Mesh(cu(p.coord), cu(p.tet.astype(np.int32)))
     cen = m.faces()["face_centroid"].cpu().numpy()
-    f = cu(np.asarray(p.f(cen), np.float64))
-    v1, r1 = m.assemble(cu(p.a), p.c, f)
-    vs, rs = m.assemble(cu(p.a * scale), p.c * scale, f)
-    x1, it1, _, _ = ph.Schwarz(m, v1).solve(v1, r1, rtol=1e-12)
-    xs, its, _, _ = ph.Schwarz(m, vs, precision="dw").solve(vs, rs, rtol=1e-12)
-    print(f"scale {scale:g}: {its} iterations (unscaled, fp64 blocks: {it1})")
-    assert abs(its - it1) <= 8
-    assert torch.allclose(xs, x1, rtol=1e-9, atol=0)
+    values, _ = m.assemble(cu(p.a), 1e-32, cu(np.asarray(p.f(cen), np.float64)))
+    with pytest.raises(ph.PHError) as e:
+        ph.Schwarz(m, values, precision="f32")
+    assert e.value.name == "PH_ERR_ARG"
+    assert "fp32 range" in ph.load().ph_last_error_message().decode()
+    P = ph.Schwarz(m, values)
+    P.close()
     m.close()
