@@ -56,11 +56,11 @@ __device__ __forceinline__ bool last_block(unsigned* done) {
 
 // z = M r for the edge-patch Schwarz preconditioner P (y: scratch of
 // P->nmem doubles), with the sum r.z: init sets rz, otherwise the last block
-// sets beta and rz.  Two launches.  With fp32 blocks the patch solves run in
-// fp32 on r scaled by a power of two near 1/sqrt(r.r) (sc->rr, set before),
-// and beta is the flexible one, -alpha z.q / rz_old (q = H p, unused at init).
-cudaError_t schwarz_apply(const ph_schwarz* P, const double* r, const double* q, double* z, double* y, double* part,
-                          Scalars* sc, bool init, cudaStream_t s);
+// sets beta = r.z / rz_old and rz.  Two launches.  With fp32 blocks the patch
+// solves run in fp32 on r scaled by a power of two near 1/sqrt(r.r) (sc->rr,
+// set before), and the sums of z in fp64.
+cudaError_t schwarz_apply(const ph_schwarz* P, const double* r, double* z, double* y, double* part, Scalars* sc,
+                          bool init, cudaStream_t s);
 
 }  // namespace ph_pcg
 

@@ -217,60 +217,22 @@ __global__ void k_mult_to_face(const int32_t* __restrict__ face_mult, int64_t nF
   if (F < nF && face_mult[F] >= 0) m2f[face_mult[F]] = (int)F;
 }
 
-// The shift k with |r_i| 2^k <= sqrt(2) for every entry of a residual of
-// squared norm rr (0 for rr zero, subnormal or not finite): fp32 patch solves
-// then see entries of magnitude <= 1.5.
-__device__ __forceinline__ int residual_shift(double rr) {
-  const int f = (__double2hiint(rr) >> 20) & 0x7FF;  // rr >= 0
-  if (f == 0 || f == 0x7FF) return 0;
-  const int e = f - 1023;  // rr in [2^e, 2^(e+1))
-  return -((e >> 1) + 1);
-}
-
-// x 2^k rounded to nearest fp32 with integer instructions (on this part the
-// F2F conversions issue on the FP64 pipe, at its rate); results below 2^-126
-// flush to zero.  |x| 2^k < 2^127.
-__device__ __forceinline__ float to_f32(double x, int k) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const int f = (int)((b >> 52) & 0x7FF);
-  const int e = f - 1023 + k;
-  if (f == 0 || e < -126) return __uint_as_float(sign);
-  const unsigned m = (unsigned)(b >> 29) & 0x7FFFFFu;  // the top 23 fraction bits
-  const unsigned rest = (unsigned)b & 0x1FFFFFFFu;     // the other 29
-  const unsigned up = rest > 0x10000000u || (rest == 0x10000000u && (m & 1u));  // to nearest even
-  return __uint_as_float(sign | ((((unsigned)(e + 127) << 23) | m) + up));
-}
-
-// x 2^k as fp64 with integer instructions (exact; x finite, the result normal).
-__device__ __forceinline__ double to_f64(float x, int k) {
-  const unsigned b = __float_as_uint(x);
-  const unsigned f = (b >> 23) & 0xFFu;
-  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
-  if (f == 0) return __longlong_as_double((long long)sign);
-  const unsigned long long ex = (unsigned long long)((int)f - 127 + k + 1023);
-  return __longlong_as_double((long long)(sign | (ex << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
-}
-
 __device__ __forceinline__ float mad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double mad(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-__device__ __forceinline__ double load_r(const double* r, int64_t i, int, double) { return __ldg(r + i); }
-__device__ __forceinline__ float load_r(const double* r, int64_t i, int k, float) { return to_f32(__ldg(r + i), k); }
-
 // y = block^-1 r_patch for one patch of K members (slot-major group arrays,
 // stride n): the packed inverse in registers, sums in member order.  T: the
-// blocks' and y's type; for float, r enters scaled by 2^k.
+// blocks' and y's type; for float, r enters scaled by rs (a power of two).
 template <int K, typename T>
 __device__ __forceinline__ void patch_solve(int64_t s, int64_t n, const int32_t* __restrict__ mem,
-                                            const T* __restrict__ blk, const double* __restrict__ r, int k,
+                                            const T* __restrict__ blk, const double* __restrict__ r, double rs,
                                             T* __restrict__ y) {
   constexpr int NQ = K * (K + 1) / 2;
   T m[NQ], rv[K];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) m[q] = __ldcs(blk + q * n + s);
 #pragma unroll
-  for (int j = 0; j < K; ++j) rv[j] = load_r(r, __ldg(mem + j * n + s), k, T());
+  for (int j = 0; j < K; ++j) rv[j] = (T)(__ldg(r + __ldg(mem + j * n + s)) * rs);
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     T v = 0;
@@ -280,6 +242,14 @@ __device__ __forceinline__ void patch_solve(int64_t s, int64_t n, const int32_t*
   }
 }
 
+// The power of two nearest above 1/sqrt(rr) (1 for rr = 0): fp32 patch
+// solves then see residual entries of magnitude <= 1.
+__device__ __forceinline__ double residual_scale(double rr) {
+  if (!(rr > 0.0) || !(rr < 1e300)) return 1.0;
+  const int e = ((__double2hiint(rr) >> 20) & 0x7FF) - 1023;  // rr in [2^e, 2^(e+1))
+  return ldexp(1.0, -(e >> 1) - 1);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_schwarz_patch(SchwarzGroups g, int64_t npatch,
                                                        const int32_t* __restrict__ mem, const T* __restrict__ blk,
@@ -287,24 +257,24 @@ __global__ void __launch_bounds__(256) k_schwarz_patch(SchwarzGroups g, int64_t 
                                                        T* __restrict__ y) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= npatch) return;
-  const int sh = sizeof(T) == sizeof(float) ? residual_shift(sc->rr) : 0;
+  const double rs = sizeof(T) == sizeof(float) ? residual_scale(sc->rr) : 1.0;
   const int k = group_of(g, t);
   const int64_t s = t - g.first[k], n = g.count[k];
   const int32_t* mm = mem + g.mbase[k];
   const T* bb = blk + g.bbase[k];
   T* yy = y + g.mbase[k];
   switch (k) {  // uniform across a warp except at the group boundaries
-    case 1: patch_solve<1>(s, n, mm, bb, r, sh, yy); break;
-    case 2: patch_solve<2>(s, n, mm, bb, r, sh, yy); break;
-    case 3: patch_solve<3>(s, n, mm, bb, r, sh, yy); break;
-    case 4: patch_solve<4>(s, n, mm, bb, r, sh, yy); break;
-    case 5: patch_solve<5>(s, n, mm, bb, r, sh, yy); break;
-    case 6: patch_solve<6>(s, n, mm, bb, r, sh, yy); break;
-    case 7: patch_solve<7>(s, n, mm, bb, r, sh, yy); break;
-    case 8: patch_solve<8>(s, n, mm, bb, r, sh, yy); break;
+    case 1: patch_solve<1>(s, n, mm, bb, r, rs, yy); break;
+    case 2: patch_solve<2>(s, n, mm, bb, r, rs, yy); break;
+    case 3: patch_solve<3>(s, n, mm, bb, r, rs, yy); break;
+    case 4: patch_solve<4>(s, n, mm, bb, r, rs, yy); break;
+    case 5: patch_solve<5>(s, n, mm, bb, r, rs, yy); break;
+    case 6: patch_solve<6>(s, n, mm, bb, r, rs, yy); break;
+    case 7: patch_solve<7>(s, n, mm, bb, r, rs, yy); break;
+    case 8: patch_solve<8>(s, n, mm, bb, r, rs, yy); break;
     default: {  // 9..kSchwarzDense members: rare; the block read entry by entry
       T rv[kSchwarzDense];
-      for (int j = 0; j < k; ++j) rv[j] = load_r(r, __ldg(mm + j * n + s), sh, T());
+      for (int j = 0; j < k; ++j) rv[j] = (T)(__ldg(r + __ldg(mm + j * n + s)) * rs);
       for (int i = 0; i < k; ++i) {
         T v = 0;
         for (int j = 0; j < k; ++j) v = mad(__ldg(bb + (int64_t)(i <= j ? upper(i, j, k) : upper(j, i, k)) * n + s),
@@ -316,44 +286,30 @@ __global__ void __launch_bounds__(256) k_schwarz_patch(SchwarzGroups g, int64_t 
 }
 
 // z = sum of the three patch values of each multiplier (fixed order), r.z;
-// the last block sets rz (init) or beta and rz.  fp64 blocks: beta = r.z /
-// rz_old.  fp32 blocks (y scaled by 2^sh, summed in fp32): the flexible
-// (Polak-Ribiere) beta = z.(r - r_old) / rz_old = -alpha z.q / rz_old, which
-// keeps conjugate gradients converging when the preconditioner's rounding
-// varies with r; z.q is summed beside r.z (q = H p of this iteration).
+// the last block sets rz (init) or beta = r.z / rz_old and rz.
 template <typename T>
 __global__ void __launch_bounds__(RT) k_schwarz_face(int64_t L, const int32_t* __restrict__ fslot,
                                                      const T* __restrict__ y, const double* __restrict__ r,
-                                                     const double* __restrict__ q, double* __restrict__ z,
-                                                     double* __restrict__ part, Scalars* __restrict__ sc, bool init) {
-  constexpr bool F32 = sizeof(T) == sizeof(float);
-  const int sh = F32 ? residual_shift(sc->rr) : 0;
-  double rz = 0.0, zq = 0.0;
+                                                     double* __restrict__ z, double* __restrict__ part,
+                                                     Scalars* __restrict__ sc, bool init) {
+  const double us = sizeof(T) == sizeof(float) ? 1.0 / residual_scale(sc->rr) : 1.0;  // exact
+  double rz = 0.0;
   for (int64_t l = blockIdx.x * (int64_t)RT + threadIdx.x; l < L; l += (int64_t)RB * RT) {
     const int s0 = fslot[3 * l], s1 = fslot[3 * l + 1], s2 = fslot[3 * l + 2];
-    double zl;
-    if (F32) zl = to_f64((float)((y[s0] + y[s1]) + y[s2]), -sh);
-    else zl = ((double)y[s0] + (double)y[s1]) + (double)y[s2];
+    const double zl = (((double)y[s0] + (double)y[s1]) + (double)y[s2]) * us;
     z[l] = zl;
     rz = fma(r[l], zl, rz);
-    if (F32 && !init) zq = fma(q[l], zl, zq);
   }
   rz = block_sum(rz);
   if (threadIdx.x == 0) part[RB + blockIdx.x] = rz;
-  if (F32 && !init) {
-    zq = block_sum(zq);
-    if (threadIdx.x == 0) part[blockIdx.x] = zq;  // p.q's partials were consumed by alpha
-  }
   if (last_block(&sc->done)) {
     const double rz_t = sum_partials(part, RB);
-    const double zq_t = F32 && !init ? sum_partials(part, 0) : 0.0;
     if (threadIdx.x == 0) {
       if (init) {
         sc->beta = 0.0;
       } else {
         const double rz_old = sc->rz;
-        const double num = F32 ? -sc->alpha * zq_t : rz_t;
-        sc->beta = rz_old > 0.0 ? num / rz_old : 0.0;
+        sc->beta = rz_old > 0.0 ? rz_t / rz_old : 0.0;
       }
       sc->rz = rz_t;
       sc->done = 0;
@@ -365,17 +321,17 @@ __global__ void __launch_bounds__(RT) k_schwarz_face(int64_t L, const int32_t* _
 
 namespace ph_pcg {
 
-cudaError_t schwarz_apply(const ph_schwarz* P, const double* r, const double* q, double* z, double* y, double* part,
-                          Scalars* sc, bool init, cudaStream_t s) {
+cudaError_t schwarz_apply(const ph_schwarz* P, const double* r, double* z, double* y, double* part, Scalars* sc,
+                          bool init, cudaStream_t s) {
   if (P->blk32) {  // fp32 patch values in the first half of y's scratch
     float* y32 = reinterpret_cast<float*>(y);
     if (P->npatch > 0)
       k_schwarz_patch<float><<<ph::grid_for(P->npatch), 256, 0, s>>>(P->g, P->npatch, P->mem, P->blk32, r, sc, y32);
-    k_schwarz_face<float><<<RB, RT, 0, s>>>(P->L, P->fslot, y32, r, q, z, part, sc, init);
+    k_schwarz_face<float><<<RB, RT, 0, s>>>(P->L, P->fslot, y32, r, z, part, sc, init);
   } else {
     if (P->npatch > 0)
       k_schwarz_patch<double><<<ph::grid_for(P->npatch), 256, 0, s>>>(P->g, P->npatch, P->mem, P->blk, r, sc, y);
-    k_schwarz_face<double><<<RB, RT, 0, s>>>(P->L, P->fslot, y, r, q, z, part, sc, init);
+    k_schwarz_face<double><<<RB, RT, 0, s>>>(P->L, P->fslot, y, r, z, part, sc, init);
   }
   return ph::launched(P->npatch > 0 ? 2 : 1);
 }

@@ -277,7 +277,7 @@ inline cudaError_t pcg_iteration(int64_t n, const Matrix& A, double* x, double* 
   if (vec) k_update<true, false><<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
   else k_update<false, false><<<RB, RT, 0, s>>>(n, x, r, p, q, dinv, sc, part);
   cudaError_t e = ph::launched(2);
-  if (e == cudaSuccess) e = schwarz_apply(P, r, q, dinv, y, part, sc, false, s);
+  if (e == cudaSuccess) e = schwarz_apply(P, r, dinv, y, part, sc, false, s);
   if (e == cudaSuccess) {
     k_direction_z<<<RB, RT, 0, s>>>(n, p, dinv, sc);
     e = ph::launched();
@@ -327,7 +327,7 @@ ph_status pcg_run(int64_t n, const int32_t* rowptr, const int32_t* colind, const
     e = ph::launched();
   }
   if (e == cudaSuccess && P) {  // z = M b, p = z
-    e = schwarz_apply(P, r, nullptr, dinv, y, part, sc, true, s);
+    e = schwarz_apply(P, r, dinv, y, part, sc, true, s);
     if (e == cudaSuccess) {
       k_direction_z<<<RB, RT, 0, s>>>(n, p, dinv, sc);
       e = ph::launched();

@@ -186,9 +186,8 @@ def test_fp32_blocks_out_of_range(ph):
     blocks' range: ph_schwarz_create_f32 refuses with PH_ERR_ARG and says so;
     the fp64 blocks still solve."""
     p = make("sin_kuhn")
-    m = ph.Mesh(cu(p.coord), cu(p.tet.astype(np.int32)))
-    cen = m.faces()["face_centroid"].cpu().numpy()
-    values, _ = m.assemble(cu(p.a), 1e-32, cu(np.asarray(p.f(cen), np.float64)))
+    p.c = 1e-32
+    m, values, rhs, _, _, _ = system(ph, p)
     with pytest.raises(ph.PHError) as e:
         ph.Schwarz(m, values, precision="f32")
     assert e.value.name == "PH_ERR_ARG"
