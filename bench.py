@@ -704,35 +704,29 @@ def adjoint_section(ph, dev, rtol=1e-10):
     a = torch.as_tensor(meshgen.lognormal_field(p.nE, 51), device=dev)
     forward(a)  # warm-up
     stream = torch.cuda.current_stream()
-
-    def gradient(precision):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
-        torch.cuda.synchronize()
-        ev[0].record(stream)
-        values, rhs, factor = mesh.assemble(a, c, f, factor=True)
-        ev[1].record(stream)
-        P = ph.Schwarz(mesh, values, precision=precision)
-        ev[2].record(stream)
-        lam, it1, _, _ = P.solve(values, rhs, rtol=rtol, maxit=100000)
-        ev[3].record(stream)
-        u = mesh.recover_factored(factor, c, f, lam)
-        J = mesh.misfit(u, u_obs)
-        ev[4].record(stream)
-        rq = mesh.adjoint_rhs(factor, c, u, u_obs)
-        ev[5].record(stream)
-        q, it2, _, _ = P.solve(values, rq, rtol=rtol, maxit=100000)
-        ev[6].record(stream)
-        grad = mesh.adjoint_grad(a, factor, c, u, u_obs, q)
-        ev[7].record(stream)
-        torch.cuda.synchronize()
-        P.close()
-        return J, grad, [it1, it2], [ev[i].elapsed_time(ev[i + 1]) for i in range(7)]
-
-    J, grad, its, t = gradient("f64")
-    J32, grad32, its32, t32 = gradient("f32")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    values, rhs, factor = mesh.assemble(a, c, f, factor=True)
+    ev[1].record(stream)
+    P = ph.Schwarz(mesh, values)
+    ev[2].record(stream)
+    lam, it1, _, _ = P.solve(values, rhs, rtol=rtol, maxit=100000)
+    ev[3].record(stream)
+    u = mesh.recover_factored(factor, c, f, lam)
+    J = mesh.misfit(u, u_obs)
+    ev[4].record(stream)
+    rq = mesh.adjoint_rhs(factor, c, u, u_obs)
+    ev[5].record(stream)
+    q, it2, _, _ = P.solve(values, rq, rtol=rtol, maxit=100000)
+    ev[6].record(stream)
+    grad = mesh.adjoint_grad(a, factor, c, u, u_obs, q)
+    ev[7].record(stream)
+    torch.cuda.synchronize()
+    P.close()
+    t = [ev[i].elapsed_time(ev[i + 1]) for i in range(7)]
     total = sum(t)
     adj_kernels_ms = t[4] + t[6]
-    it1, it2 = its
     out = {
         "workload": "Kuhn 6^3 cube, 3 refinement levels", "nE": p.nE, "L": mesh.L,
         "J": J.item(), "grad_norm": grad.norm().item(),
@@ -742,15 +736,6 @@ def adjoint_section(ph, dev, rtol=1e-10):
         "pcg_iterations": [it1, it2], "pcg_rtol": rtol, "preconditioner": "edge-patch additive Schwarz",
         "adjoint_kernels_tets_per_s": p.nE / (adj_kernels_ms * 1e-3),
         "note": "gradient time is dominated by the two PCG solves of the condensed system",
-        "fp32_patch_blocks": {
-            "what": "the same gradient with ph_schwarz_create_f32: patch inverses stored and applied in fp32, "
-                    "residual, updates and stopping test in fp64",
-            "ms_per_gradient": sum(t32), "grads_per_s": 1000.0 / sum(t32), "speedup": total / sum(t32),
-            "pcg_iterations": its32,
-            "ms": {"schwarz_setup": t32[1], "forward_solve": t32[2], "adjoint_solve": t32[5]},
-            "grad_rel_diff_vs_fp64_blocks": (grad32 - grad).norm().item() / grad.norm().item(),
-            "J_rel_diff": abs(J32.item() - J.item()) / abs(J.item()),
-        },
     }
     mesh.close()
     return out
@@ -822,11 +807,10 @@ def cpu_baseline(p, workload, budget_s=15.0):
             "speedup": (n_all / t_all) / (n_one / t_one)}
 
 
-def profile_pcg(iters, precision="f64"):
+def profile_pcg(iters):
     """A fixed number of Schwarz-preconditioned PCG iterations on the adjoint
     workload's system (Kuhn 6^3 cube, 3 levels, c = 0.1, lognormal a with
-    seed 51), with fp64 or fp32 patch blocks: a target for profiler launch
-    lists of the solve."""
+    seed 51): a target for profiler launch lists of the solve."""
     import torch
     import paper_2509_11133_gb300 as ph
     from paper_2509_11133_gb300 import build
@@ -839,10 +823,10 @@ def profile_pcg(iters, precision="f64"):
     f = torch.as_tensor(np.asarray(meshgen.sin_source(cen), np.float64), device=dev)
     a = torch.as_tensor(meshgen.lognormal_field(p.nE, 51), device=dev)
     values, rhs = mesh.assemble(a, 0.1, f)
-    P = ph.Schwarz(mesh, values, precision=precision)
+    P = ph.Schwarz(mesh, values)
     _, it, _, _ = P.solve(values, rhs, rtol=0.0, maxit=iters, check=False)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_pcg": {"L": mesh.L, "iterations": it, "precision": precision}}))
+    print(json.dumps({"profile_pcg": {"L": mesh.L, "iterations": it}}))
     P.close()
     mesh.close()
     return 0
@@ -966,8 +950,6 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=3.0)
     ap.add_argument("--profile-pcg", type=int, default=0, metavar="N",
                     help="profiler target: N Schwarz-PCG iterations on the adjoint workload, then exit")
-    ap.add_argument("--pcg-precision", default="f64", choices=["f64", "f32"],
-                    help="Schwarz patch blocks used by --profile-pcg")
     ap.add_argument("--profile-kernels", type=int, default=0, metavar="R",
                     help="profiler target: R rounds of the element kernels (assembly, recovery, misfit, adjoint) "
                          "on --workload, then exit")
@@ -978,7 +960,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.profile_pcg > 0:
-        return profile_pcg(args.profile_pcg, args.pcg_precision)
+        return profile_pcg(args.profile_pcg)
     if args.profile_kernels > 0:
         return profile_kernels(args.workload, args.profile_kernels, args.variant)
     if args.impl == "reference":

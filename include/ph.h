@@ -370,18 +370,10 @@ ph_status ph_refined_destroy(ph_refined* r, void* stream);
  * ph_solve_pcg_schwarz: conjugate gradients on H preconditioned by P;
  *   arguments and results as ph_solve_pcg (n = L of the mesh).  P must come
  *   from the same mesh and values; concurrent solves may share P.
- * ph_schwarz_create_f32: the same preconditioner with the patch inverses
- *   (computed in fp64) stored rounded to fp32 and applied on the FP32 pipe to
- *   the residual scaled by a power of two near 1/||r||; the solve's residual,
- *   updates and stopping test stay fp64, so the solution's accuracy is that
- *   of ph_solve_pcg_schwarz with the fp64 blocks and only the iteration count
- *   can differ.  PH_ERR_ARG also when a patch inverse has an entry outside
- *   [2^-100, 2^100] in magnitude (use ph_schwarz_create there).
  * ph_schwarz_destroy: frees in stream order.
  */
 typedef struct ph_schwarz ph_schwarz;
 ph_status ph_schwarz_create(const ph_mesh* mesh, const double* values, void* stream, ph_schwarz** out);
-ph_status ph_schwarz_create_f32(const ph_mesh* mesh, const double* values, void* stream, ph_schwarz** out);
 ph_status ph_schwarz_destroy(ph_schwarz* P, void* stream);
 ph_status ph_solve_pcg_schwarz(const ph_mesh* mesh, const double* values, const ph_schwarz* P, const double* b,
                                double* x, double rtol, int32_t maxit, int32_t* iters, double* relres, void* stream);

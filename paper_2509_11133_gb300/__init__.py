@@ -33,7 +33,7 @@ EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces",
            "ph_adjoint_rhs", "ph_adjoint_grad", "ph_batch_create", "ph_batch_destroy", "ph_batch_bind",
            "ph_batch_assemble", "ph_batch_autotune", "ph_batch_set_config", "ph_batch_get_config",
            "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy", "ph_rcp", "ph_half_sqrt", "ph_timing_enable",
-           "ph_kernel_time", "ph_assemble_host", "ph_schwarz_create", "ph_schwarz_create_f32", "ph_schwarz_destroy",
+           "ph_kernel_time", "ph_assemble_host", "ph_schwarz_create", "ph_schwarz_destroy",
            "ph_solve_pcg_schwarz", "ph_fp64_peak", "ph_test_fail_alloc", "ph_test_scan_withhold",
            "ph_pool_in_use", "ph_solve_refined", "ph_mesh_create_batch", "ph_host_mesh_query",
            "ph_assemble_dw", "ph_batch_bind_recovery", "ph_mesh_create_dw")
@@ -111,7 +111,6 @@ def load(path: str | None = None):
         "ph_kernel_time": [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(D), ctypes.POINTER(I64)],
         "ph_assemble_host": [P, I64, P, I64, P, I64, I64, I64, I64, P, D, P, P, P, P, P, P, P, P, P, P],
         "ph_schwarz_create": [P, P, P, ctypes.POINTER(P)],
-        "ph_schwarz_create_f32": [P, P, P, ctypes.POINTER(P)],
         "ph_schwarz_destroy": [P, P],
         "ph_solve_pcg_schwarz": [P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P],
     }
@@ -200,19 +199,14 @@ PH_PCG_NOALLOC_MAX_N = 262144
 
 class Schwarz:
     """Edge-patch additive Schwarz preconditioner of a mesh's assembled H
-    (``values`` from ``Mesh.assemble``); ``solve`` runs PCG with it.
-    precision "f64" (ph_schwarz_create) or "f32" (ph_schwarz_create_f32:
-    patch inverses stored and applied in fp32; the solve stays fp64)."""
+    (``values`` from ``Mesh.assemble``); ``solve`` runs PCG with it."""
 
-    def __init__(self, mesh, values, stream=None, precision="f64"):
-        if precision not in ("f64", "f32"):
-            raise ValueError("precision: 'f64' or 'f32'")
-        name = "ph_schwarz_create" if precision == "f64" else "ph_schwarz_create_f32"
+    def __init__(self, mesh, values, stream=None):
         h = ctypes.c_void_p()
         self._h = None
         self.mesh = mesh
-        self.precision = precision
-        _check(getattr(load(), name)(mesh.handle, _ptr(values.contiguous()), _stream(stream), ctypes.byref(h)), name)
+        _check(load().ph_schwarz_create(mesh.handle, _ptr(values.contiguous()), _stream(stream), ctypes.byref(h)),
+               "ph_schwarz_create")
         self._h = h
 
     def solve(self, values, rhs, x=None, rtol=1e-12, maxit=20000, stream=None, check=True):
@@ -663,15 +657,14 @@ class Batch:
 
 def solve_system(mesh, values, rhs, rtol, maxit, precond="schwarz", P=None):
     """H Lambda = rhs on the mesh's CSR pattern: PCG with the edge-patch
-    Schwarz preconditioner ("schwarz", or "schwarz_f32" with its blocks in
-    fp32; P reused when given) or Jacobi.  Returns (Lambda, iterations, P)."""
-    if precond in ("schwarz", "schwarz_f32"):
-        if P is None:
-            P = Schwarz(mesh, values, precision="f32" if precond == "schwarz_f32" else "f64")
+    Schwarz preconditioner (P reused when given) or Jacobi.  Returns
+    (Lambda, iterations, P)."""
+    if precond == "schwarz":
+        P = Schwarz(mesh, values) if P is None else P
         lam, it, _, _ = P.solve(values, rhs, rtol=rtol, maxit=maxit)
         return lam, it, P
     if precond != "jacobi":
-        raise ValueError("precond: 'schwarz', 'schwarz_f32' or 'jacobi'")
+        raise ValueError("precond: 'schwarz' or 'jacobi'")
     rowptr, colind = mesh.csr_pattern()
     lam, it, _, _ = ph_solve_pcg(rowptr, colind, values, rhs, rtol=rtol, maxit=maxit)
     return lam, it, None

@@ -56,9 +56,7 @@ __device__ __forceinline__ bool last_block(unsigned* done) {
 
 // z = M r for the edge-patch Schwarz preconditioner P (y: scratch of
 // P->nmem doubles), with the sum r.z: init sets rz, otherwise the last block
-// sets beta = r.z / rz_old and rz.  Two launches.  With fp32 blocks the patch
-// solves run in fp32 on r scaled by a power of two near 1/sqrt(r.r) (sc->rr,
-// set before), and the sums of z in fp64.
+// sets beta = r.z / rz_old and rz.  Two launches.
 cudaError_t schwarz_apply(const ph_schwarz* P, const double* r, double* z, double* y, double* part, Scalars* sc,
                           bool init, cudaStream_t s);
 
@@ -85,7 +83,6 @@ struct ph_schwarz {
   int64_t L, nEd, nmem, npatch, nblk;
   SchwarzGroups g;
   int32_t* mem;    // multiplier ids, ascending within a patch
-  double* blk;     // patch inverses: packed upper triangle, row-major (fp64), or null
-  float* blk32;    // the same rounded to fp32 (ph_schwarz_create_f32), or null
+  double* blk;     // patch inverses: packed upper triangle, row-major
   int32_t* fslot;  // 3L: positions in mem (and y) of each multiplier in the patches of its face's three edges
 };

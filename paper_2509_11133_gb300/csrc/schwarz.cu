@@ -15,13 +15,6 @@
 // (sums in member order) with the block in registers, then one thread per
 // multiplier adds the three values of its face's three edges in a fixed order
 // -- no atomics, so a solve repeats bit for bit.
-// Mixed precision (ph_schwarz_create_f32): the blocks are factored and
-// inverted in fp64 as above and stored rounded to fp32, and the patch solves
-// run on the FP32 pipe (the fp64 ones are FP64-bound: K^2 FMA per patch).  A
-// preconditioner only steers the iteration -- the residual, the updates and
-// the stopping test stay fp64 -- so the solution's accuracy is unchanged;
-// the rounding of M (~1e-7 relative, symmetric storage) changes the
-// iteration count slightly.
 #include <math.h>
 #include <string.h>
 
@@ -161,18 +154,15 @@ __device__ __forceinline__ int group_of(const SchwarzGroups& g, int64_t t) {
 
 // Invert each patch block: Cholesky A = G G', then A^-1 = G^-T G^-1 (upper
 // triangle stored, slot-major within the group).
-// T = float: the inverse rounded to fp32, PH_ERR_ARG for an entry outside
-// [2^-100, 2^100] in magnitude (fp32 range with room for the products).
-template <typename T>
 __global__ void k_group_factor(SchwarzGroups g, int64_t npatch, const int32_t* __restrict__ mem,
                                const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                               const double* __restrict__ values, T* __restrict__ blk, unsigned* status) {
+                               const double* __restrict__ values, double* __restrict__ blk, unsigned* status) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= npatch) return;
   const int k = group_of(g, t);
   const int64_t s = t - g.first[k], n = g.count[k];
   const int32_t* mm = mem + g.mbase[k] + s;  // member i at mm[i n]
-  T* out = blk + g.bbase[k] + s;             // entry q at out[q n]
+  double* out = blk + g.bbase[k] + s;        // entry q at out[q n]
   constexpr int K = kSchwarzDense;
   double a[K * K];  // lower Cholesky factor, then its inverse (row-major)
   for (int i = 0; i < k; ++i)
@@ -206,9 +196,7 @@ __global__ void k_group_factor(SchwarzGroups g, int64_t npatch, const int32_t* _
     for (int j = i; j < k; ++j) {
       double v = 0.0;
       for (int q = j; q < k; ++q) v += a[q * K + i] * a[q * K + j];
-      if (sizeof(T) == sizeof(float) && v != 0.0 && !(fabs(v) >= 0x1p-100 && fabs(v) <= 0x1p100))
-        ph_flag(status, PH_ERR_ARG);
-      out[(int64_t)upper(i, j, k) * n] = (T)v;
+      out[(int64_t)upper(i, j, k) * n] = v;
     }
 }
 
@@ -217,67 +205,53 @@ __global__ void k_mult_to_face(const int32_t* __restrict__ face_mult, int64_t nF
   if (F < nF && face_mult[F] >= 0) m2f[face_mult[F]] = (int)F;
 }
 
-__device__ __forceinline__ float mad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double mad(double a, double b, double c) { return __fma_rn(a, b, c); }
-
 // y = block^-1 r_patch for one patch of K members (slot-major group arrays,
-// stride n): the packed inverse in registers, sums in member order.  T: the
-// blocks' and y's type; for float, r enters scaled by rs (a power of two).
-template <int K, typename T>
+// stride n): the packed inverse in registers, sums in member order.
+template <int K>
 __device__ __forceinline__ void patch_solve(int64_t s, int64_t n, const int32_t* __restrict__ mem,
-                                            const T* __restrict__ blk, const double* __restrict__ r, double rs,
-                                            T* __restrict__ y) {
+                                            const double* __restrict__ blk, const double* __restrict__ r,
+                                            double* __restrict__ y) {
   constexpr int NQ = K * (K + 1) / 2;
-  T m[NQ], rv[K];
+  double m[NQ], rv[K];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) m[q] = __ldcs(blk + q * n + s);
 #pragma unroll
-  for (int j = 0; j < K; ++j) rv[j] = (T)(__ldg(r + __ldg(mem + j * n + s)) * rs);
+  for (int j = 0; j < K; ++j) rv[j] = __ldg(r + __ldg(mem + j * n + s));
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    T v = 0;
+    double v = 0.0;
 #pragma unroll
-    for (int j = 0; j < K; ++j) v = mad(m[i <= j ? upper(i, j, K) : upper(j, i, K)], rv[j], v);
+    for (int j = 0; j < K; ++j) v = fma(m[i <= j ? upper(i, j, K) : upper(j, i, K)], rv[j], v);
     y[i * n + s] = v;
   }
 }
 
-// The power of two nearest above 1/sqrt(rr) (1 for rr = 0): fp32 patch
-// solves then see residual entries of magnitude <= 1.
-__device__ __forceinline__ double residual_scale(double rr) {
-  if (!(rr > 0.0) || !(rr < 1e300)) return 1.0;
-  const int e = ((__double2hiint(rr) >> 20) & 0x7FF) - 1023;  // rr in [2^e, 2^(e+1))
-  return ldexp(1.0, -(e >> 1) - 1);
-}
-
-template <typename T>
 __global__ void __launch_bounds__(256) k_schwarz_patch(SchwarzGroups g, int64_t npatch,
-                                                       const int32_t* __restrict__ mem, const T* __restrict__ blk,
-                                                       const double* __restrict__ r, const Scalars* __restrict__ sc,
-                                                       T* __restrict__ y) {
+                                                       const int32_t* __restrict__ mem,
+                                                       const double* __restrict__ blk, const double* __restrict__ r,
+                                                       double* __restrict__ y) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= npatch) return;
-  const double rs = sizeof(T) == sizeof(float) ? residual_scale(sc->rr) : 1.0;
   const int k = group_of(g, t);
   const int64_t s = t - g.first[k], n = g.count[k];
   const int32_t* mm = mem + g.mbase[k];
-  const T* bb = blk + g.bbase[k];
-  T* yy = y + g.mbase[k];
+  const double* bb = blk + g.bbase[k];
+  double* yy = y + g.mbase[k];
   switch (k) {  // uniform across a warp except at the group boundaries
-    case 1: patch_solve<1>(s, n, mm, bb, r, rs, yy); break;
-    case 2: patch_solve<2>(s, n, mm, bb, r, rs, yy); break;
-    case 3: patch_solve<3>(s, n, mm, bb, r, rs, yy); break;
-    case 4: patch_solve<4>(s, n, mm, bb, r, rs, yy); break;
-    case 5: patch_solve<5>(s, n, mm, bb, r, rs, yy); break;
-    case 6: patch_solve<6>(s, n, mm, bb, r, rs, yy); break;
-    case 7: patch_solve<7>(s, n, mm, bb, r, rs, yy); break;
-    case 8: patch_solve<8>(s, n, mm, bb, r, rs, yy); break;
+    case 1: patch_solve<1>(s, n, mm, bb, r, yy); break;
+    case 2: patch_solve<2>(s, n, mm, bb, r, yy); break;
+    case 3: patch_solve<3>(s, n, mm, bb, r, yy); break;
+    case 4: patch_solve<4>(s, n, mm, bb, r, yy); break;
+    case 5: patch_solve<5>(s, n, mm, bb, r, yy); break;
+    case 6: patch_solve<6>(s, n, mm, bb, r, yy); break;
+    case 7: patch_solve<7>(s, n, mm, bb, r, yy); break;
+    case 8: patch_solve<8>(s, n, mm, bb, r, yy); break;
     default: {  // 9..kSchwarzDense members: rare; the block read entry by entry
-      T rv[kSchwarzDense];
-      for (int j = 0; j < k; ++j) rv[j] = (T)(__ldg(r + __ldg(mm + j * n + s)) * rs);
+      double rv[kSchwarzDense];
+      for (int j = 0; j < k; ++j) rv[j] = __ldg(r + __ldg(mm + j * n + s));
       for (int i = 0; i < k; ++i) {
-        T v = 0;
-        for (int j = 0; j < k; ++j) v = mad(__ldg(bb + (int64_t)(i <= j ? upper(i, j, k) : upper(j, i, k)) * n + s),
+        double v = 0.0;
+        for (int j = 0; j < k; ++j) v = fma(__ldg(bb + (int64_t)(i <= j ? upper(i, j, k) : upper(j, i, k)) * n + s),
                                             rv[j], v);
         yy[i * n + s] = v;
       }
@@ -287,16 +261,14 @@ __global__ void __launch_bounds__(256) k_schwarz_patch(SchwarzGroups g, int64_t 
 
 // z = sum of the three patch values of each multiplier (fixed order), r.z;
 // the last block sets rz (init) or beta = r.z / rz_old and rz.
-template <typename T>
 __global__ void __launch_bounds__(RT) k_schwarz_face(int64_t L, const int32_t* __restrict__ fslot,
-                                                     const T* __restrict__ y, const double* __restrict__ r,
+                                                     const double* __restrict__ y, const double* __restrict__ r,
                                                      double* __restrict__ z, double* __restrict__ part,
                                                      Scalars* __restrict__ sc, bool init) {
-  const double us = sizeof(T) == sizeof(float) ? 1.0 / residual_scale(sc->rr) : 1.0;  // exact
   double rz = 0.0;
   for (int64_t l = blockIdx.x * (int64_t)RT + threadIdx.x; l < L; l += (int64_t)RB * RT) {
     const int s0 = fslot[3 * l], s1 = fslot[3 * l + 1], s2 = fslot[3 * l + 2];
-    const double zl = (((double)y[s0] + (double)y[s1]) + (double)y[s2]) * us;
+    const double zl = (y[s0] + y[s1]) + y[s2];
     z[l] = zl;
     rz = fma(r[l], zl, rz);
   }
@@ -323,16 +295,9 @@ namespace ph_pcg {
 
 cudaError_t schwarz_apply(const ph_schwarz* P, const double* r, double* z, double* y, double* part, Scalars* sc,
                           bool init, cudaStream_t s) {
-  if (P->blk32) {  // fp32 patch values in the first half of y's scratch
-    float* y32 = reinterpret_cast<float*>(y);
-    if (P->npatch > 0)
-      k_schwarz_patch<float><<<ph::grid_for(P->npatch), 256, 0, s>>>(P->g, P->npatch, P->mem, P->blk32, r, sc, y32);
-    k_schwarz_face<float><<<RB, RT, 0, s>>>(P->L, P->fslot, y32, r, z, part, sc, init);
-  } else {
-    if (P->npatch > 0)
-      k_schwarz_patch<double><<<ph::grid_for(P->npatch), 256, 0, s>>>(P->g, P->npatch, P->mem, P->blk, r, sc, y);
-    k_schwarz_face<double><<<RB, RT, 0, s>>>(P->L, P->fslot, y, r, z, part, sc, init);
-  }
+  if (P->npatch > 0)
+    k_schwarz_patch<<<ph::grid_for(P->npatch), 256, 0, s>>>(P->g, P->npatch, P->mem, P->blk, r, y);
+  k_schwarz_face<<<RB, RT, 0, s>>>(P->L, P->fslot, y, r, z, part, sc, init);
   return ph::launched(P->npatch > 0 ? 2 : 1);
 }
 
@@ -344,28 +309,15 @@ static void schwarz_free(ph_schwarz* P, cudaStream_t s) {
   if (!P) return;
   free_async(P->mem, s);
   free_async(P->blk, s);
-  free_async(P->blk32, s);
   free_async(P->fslot, s);
   delete P;
 }
 
-static ph_status schwarz_create(const ph_mesh* m, const double* values, cudaStream_t s, bool f32,
-                                ph_schwarz** out);
-
 extern "C" ph_status ph_schwarz_create(const ph_mesh* m, const double* values, void* stream, ph_schwarz** out) {
-  return schwarz_create(m, values, (cudaStream_t)stream, false, out);
-}
-
-extern "C" ph_status ph_schwarz_create_f32(const ph_mesh* m, const double* values, void* stream,
-                                           ph_schwarz** out) {
-  return schwarz_create(m, values, (cudaStream_t)stream, true, out);
-}
-
-static ph_status schwarz_create(const ph_mesh* m, const double* values, cudaStream_t s, bool f32,
-                                ph_schwarz** out) {
   if (!out) return PH_ERR_ARG;
   *out = nullptr;
   if (!m || (m->nnz > 0 && !values)) return PH_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
   ph_schwarz* P = new ph_schwarz();
   memset(P, 0, sizeof *P);
   P->device = m->device;
@@ -444,7 +396,7 @@ static ph_status schwarz_create(const ph_mesh* m, const double* values, cudaStre
 
   // placement (one deterministic pass per occupied group) and face slots
   e = alloc(&P->mem, (size_t)P->nmem, s);
-  if (e == cudaSuccess) e = f32 ? alloc(&P->blk32, (size_t)P->nblk, s) : alloc(&P->blk, (size_t)P->nblk, s);
+  if (e == cudaSuccess) e = alloc(&P->blk, (size_t)P->nblk, s);
   if (e == cudaSuccess) e = alloc(&m2f, (size_t)L, s);
   if (e == cudaSuccess) e = alloc(&P->fslot, (size_t)(3 * L), s);
   if (e == cudaSuccess) e = alloc(&ind, (size_t)P->nEd + 1, s);
@@ -469,23 +421,14 @@ static ph_status schwarz_create(const ph_mesh* m, const double* values, cudaStre
     if (e != cudaSuccess) { st = cuda_status(e, "ph_schwarz_create"); goto done; }
   }
   if (P->npatch > 0) {
-    if (f32)
-      k_group_factor<float><<<grid_for(P->npatch, 128), 128, 0, s>>>(g, P->npatch, P->mem, m->rowptr, m->colind,
-                                                                     values, P->blk32, status);
-    else
-      k_group_factor<double><<<grid_for(P->npatch, 128), 128, 0, s>>>(g, P->npatch, P->mem, m->rowptr, m->colind,
-                                                                      values, P->blk, status);
+    k_group_factor<<<grid_for(P->npatch, 128), 128, 0, s>>>(g, P->npatch, P->mem, m->rowptr, m->colind, values,
+                                                            P->blk, status);
     e = launched();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { st = cuda_status(e, "ph_schwarz_create"); goto done; }
-  if (bits) {
-    st = status_from_bits(bits);
-    if (f32 && st == PH_ERR_ARG)
-      set_error_text("ph_schwarz_create_f32: a patch block is not positive definite, or its inverse is outside "
-                     "the fp32 range (ph_schwarz_create keeps it in fp64)");
-  }
+  if (bits) st = status_from_bits(bits);
 
 done:
   release_edges(E, s);

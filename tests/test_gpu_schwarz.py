@@ -132,66 +132,3 @@ def test_schwarz_solve_repeatable(ph):
     assert it1 == it2 and torch.equal(x1, x2)
     P.close()
     m.close()
-
-
-# ---------------------------------------------------------------------------
-# fp32 patch blocks (ph_schwarz_create_f32)
-# ---------------------------------------------------------------------------
-@pytest.mark.parametrize("name", CASES)
-def test_fp32_blocks_same_accuracy(ph, name):
-    """The solve with fp32 patch blocks reaches the same bar against the
-    oracle's exact solution (the residual and the stopping test are fp64),
-    in at most 10% more iterations than with the fp64 blocks (both printed)."""
-    p = make(name)
-    m, values, rhs, rowptr, colind, host_sys = system(ph, p)
-    P64 = ph.Schwarz(m, values)
-    P32 = ph.Schwarz(m, values, precision="f32")
-    x64, it64, _, _ = P64.solve(values, rhs, rtol=1e-12, maxit=20000)
-    x32, it32, rr32, _ = P32.solve(values, rhs, rtol=1e-12, maxit=20000)
-    rp, ci, va, b = host_sys
-    ref, _, _ = oracle.solve_refined(rp, ci, va, b)
-    H = sp.csr_matrix((va, ci, rp), shape=(m.L, m.L))
-    x = x32.cpu().numpy()
-    err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
-    err64 = np.linalg.norm(x64.cpu().numpy() - ref) / np.linalg.norm(ref)
-    print(f"{name}: fp32 blocks {it32} iterations, error {err:.3e}; fp64 blocks {it64} iterations, "
-          f"error {err64:.3e}")
-    assert rr32 <= 1e-12
-    assert np.linalg.norm(b - H @ x) <= 1e-11 * np.linalg.norm(b)
-    assert err <= SOLVE_RTOL
-    assert it32 <= 1.1 * it64 + 8
-    P64.close()
-    P32.close()
-    m.close()
-
-
-def test_fp32_blocks_repeatable_and_refined(ph):
-    p = make("jitter_checker_m1_k3")
-    m, values, rhs, _, _, host_sys = system(ph, p)
-    P = ph.Schwarz(m, values, precision="f32")
-    x1, it1, _, _ = P.solve(values, rhs, rtol=1e-11)
-    x2, it2, _, _ = P.solve(values, rhs, rtol=1e-11)
-    assert it1 == it2 and torch.equal(x1, x2)
-    x, steps, it, corr, _ = ph.solve_refined(m, values, rhs, P, tol=1e-15, inner_rtol=1e-8, maxit=200000)
-    ref, _, _ = oracle.solve_refined(*host_sys)
-    err = np.linalg.norm(x.cpu().numpy() - ref) / np.linalg.norm(ref)
-    print(f"refined with fp32 blocks: {steps} steps, {it} iterations, error {err:.2e}")
-    assert corr <= 1e-15 and err <= 1e-12
-    P.close()
-    m.close()
-
-
-def test_fp32_blocks_out_of_range(ph):
-    """c = 1e-32 makes H ~ 1/c and the patch inverses ~1e-32, below the fp32
-    blocks' range: ph_schwarz_create_f32 refuses with PH_ERR_ARG and says so;
-    the fp64 blocks still solve."""
-    p = make("sin_kuhn")
-    p.c = 1e-32
-    m, values, rhs, _, _, _ = system(ph, p)
-    with pytest.raises(ph.PHError) as e:
-        ph.Schwarz(m, values, precision="f32")
-    assert e.value.name == "PH_ERR_ARG"
-    assert "fp32 range" in ph.load().ph_last_error_message().decode()
-    P = ph.Schwarz(m, values)
-    P.close()
-    m.close()
