@@ -267,8 +267,8 @@ ph_status ph_solve_pcg(int64_t n, const int32_t* rowptr, const int32_t* colind, 
  * - n > PH_PCG_NOALLOC_MAX_N is rejected with PH_ERR_ARG before any GPU work;
  *   ph_last_error_message() then names the limit.
  * - The first call on a device looks up the array's device address (once per
- *   device, with that device current); make that first call before any stream
- *   capture.  The address is kept for the life of the process: like the
+ *   device, with that device current).  The address is kept for the life of
+ *   the process: like the
  *   library's memory pools, it belongs to the device's primary context, so
  *   the library must not be used across a cudaDeviceReset.  Devices 0..63
  *   only (PH_ERR_ARG, with a message, beyond).
