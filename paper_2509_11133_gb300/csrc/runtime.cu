@@ -50,6 +50,13 @@ static cudaError_t pool_for(int dev, cudaMemPool_t* out) {
     uint64_t thr = ~0ull;
     e = cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &thr);
     if (e != cudaSuccess) return e;
+    // A block freed on another stream is reused only once its free has
+    // completed, never by making this stream wait for that one: calls on
+    // different streams (several host threads) must not serialise through
+    // the pool.  The pool grows instead.
+    int no = 0;
+    e = cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolReuseAllowInternalDependencies, &no);
+    if (e != cudaSuccess) return e;
     g_pool_ok[dev] = true;
   }
   *out = g_pools[dev];
