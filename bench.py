@@ -85,11 +85,12 @@ TIMED_KERNELS = ("k_assemble", "zero_values", "k_recover_factored")
 # mesh-build kernels, timed in a separate short loop (their timers add host
 # work between the build's launches)
 BUILD_KERNELS = ("k_face_count", "k_face_fill", "k_face_match", "k_face_emit", "k_row_fill", "k_scan")
-# sources that k_assemble (both variants) is compiled from
-ASSEMBLE_SOURCES = ("assemble.cu", "element.cuh", "fp64.cuh", "dw.cuh")
 
 
-def assemble_sources_sha256(sources=ASSEMBLE_SOURCES):
+def sources_sha256(sources):
+    """sha256 over the named files of the library's csrc/, in order: the key
+    a profile summary carries, so that its figures are used only while the
+    kernels they were taken on are unchanged."""
     h = hashlib.sha256()
     for name in sources:
         with open(os.path.join(ROOT, "paper_2509_11133_gb300", "csrc", name), "rb") as fh:
@@ -109,7 +110,7 @@ def profile_kv(name):
                 kv[k.strip()] = v.strip()
     except OSError:
         return {}
-    if kv.get("sources_sha256") != assemble_sources_sha256(tuple(kv.get("sources", "").split())):
+    if kv.get("sources_sha256") != sources_sha256(kv.get("sources", "").split()):
         return {}
     return kv
 
