@@ -84,7 +84,7 @@ E_INFLIGHT = 2
 TIMED_KERNELS = ("k_assemble", "zero_values", "k_recover_factored")
 # mesh-build kernels, timed in a separate short loop (their timers add host
 # work between the build's launches)
-BUILD_KERNELS = ("k_face_insert", "k_face_emit", "k_row_fill", "k_scan")
+BUILD_KERNELS = ("k_face_count", "k_face_fill", "k_face_match", "k_face_emit", "k_row_fill", "k_scan")
 
 
 def sources_sha256(sources):

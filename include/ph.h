@@ -84,10 +84,10 @@ typedef struct {
  *           paper's Nb, Listing 1), or NULL with nN = 0.  Every other boundary
  *           face is Dirichlet.
  * Connectivity follows Section 3.3 (FacesUp) and the jump convention of
- * Section 2.2; it is computed on the device with a table of face keys
- * whose home slots are grouped by the key's largest vertex (the second
- * local face with a key finds the first), and is bit-identical to the
- * definition (first occurrence numbering).
+ * Section 2.2; it is computed on the device by bucketing face keys by their
+ * largest vertex (and two bits of the middle one) and matching within
+ * buckets, and is bit-identical to the definition (first occurrence
+ * numbering).
  * Runs in order on `stream`.  Face and CSR arrays are sized by the bounds
  * nF <= 4 nE + nN and nnz <= 16 nE + nN, so the build is enqueued at once and
  * the call blocks the host once, at the end, to read the counts and the
@@ -502,7 +502,7 @@ ph_status ph_host_mesh_query(const double* coord, int64_t nC, const int32_t* tet
  * Kernel timing, off by default.  `on` is a mask: bit 0 times k_assemble,
  * zero_values (the clearing of values and rhs), k_recover and
  * k_recover_factored; bit 1 the mesh-build kernels
- * (k_face_insert, k_face_emit, k_row_fill) and
+ * (k_face_count, k_face_fill, k_face_match, k_face_emit, k_row_fill) and
  * the scans (k_scan); 0 switches timing off.  A timed launch
  * is bracketed by a pair of CUDA events on the stream it runs on (not while
  * that stream is being captured into a graph); the events come from a pool

@@ -4,13 +4,13 @@
 //
 // Connectivity.  The paper builds faces from edge-to-tet sparse maps
 // (Listings EdgeNum2Tetra, FacesUp).  Here every local face becomes a key
-// (v0 < v1 < v2) that is inserted into an open-addressing table whose home
-// slots are grouped by the largest vertex v2 (mesh order keeps the accesses
-// local): the first local face with a key claims a slot, the second finds it
-// and the two become mates.  The result is the paper's numbering: a face's id
-// is the rank of its first occurrence in (tet, local face) order and the tet
-// of that occurrence is T+ (a scan over the tets' mates); it does not depend
-// on which of the two claimed the slot.
+// (v0 < v1 < v2) that is counting-sorted into buckets by its largest vertex v2
+// (histogram, scan, scatter; mesh order keeps the scatter local; on refined
+// meshes the largest vertex spreads keys more evenly than the smallest), and
+// the keys of a bucket are matched against each other.  The result is the
+// paper's numbering: a face's id is the rank of its first occurrence in
+// (tet, local face) order and the tet of that occurrence is T+; it does not
+// depend on the order of entries inside a bucket.
 #include <math.h>
 #include <string.h>
 
@@ -63,19 +63,14 @@ __device__ __forceinline__ int3 neumann_tri(const int32_t* nb, int64_t i) {
   return make_int3(nb[3 * i], nb[3 * i + 1], nb[3 * i + 2]);
 }
 
-// Face-key table: home slot of a sorted key (v0 < v1 < v2) = v2 * 2^lgP +
-// (a hash of v0 and v1) mod 2^lgP, then linear probing over the whole table.
-// 2^lgP > 4 nE / nC, so the table has more slots than there are local faces
-// and every probe sequence ends.  A slot holds 1 + the claiming local face's
-// slot id (4t + k), 0 when empty.  Hashing v0 as well as v1 matters: the
-// faces around one edge (v1, v2) share both vertices.
-__device__ __forceinline__ int64_t key_home(int3 s, int lgP) {
-  unsigned h = (unsigned)s.x * 0x9E3779B1u + (unsigned)s.y * 0x85EBCA77u;
-  h ^= h >> 15;
-  return ((int64_t)s.z << lgP) | (int64_t)(h & ((1u << lgP) - 1u));
+// Bucket of a sorted face key (v0 < v1 < v2): the largest vertex and `sub`
+// bits hashed from the other two, so a bucket holds about 2^-sub of the faces
+// whose largest vertex is v2.  Hashing v0 as well as v1 matters: the faces
+// around one edge (v1, v2) share both vertices, and bits of v1 alone leave
+// them all in one bucket (long match scans).
+__device__ __forceinline__ int64_t bucket_of(int3 s, int sub) {
+  return ((int64_t)s.z << sub) | ((s.x ^ s.y) & ((1 << sub) - 1));
 }
-
-__device__ __forceinline__ bool same_key(int3 a, int3 b) { return a.x == b.x && a.y == b.y && a.z == b.z; }
 
 // Element geometry record of tet t (fp64; compute_geo): G_e, G_e T0^-1,
 // |det E|, 1/|det E|.
@@ -173,76 +168,123 @@ __device__ __forceinline__ void tet_geom_dw(const double* __restrict__ coord, in
   for (int i = 0; i < 9; ++i) o[i] = make_float4(out[4 * i], out[4 * i + 1], out[4 * i + 2], out[4 * i + 3]);
 }
 
-// 1. every local face of every tet into the key table.  A face whose key is
-//    new claims the empty slot; one that finds its key claimed becomes the
-//    claimer's mate (mate[claimer] by compare-and-swap from -1, so a third
-//    local face with that key finds it taken: PH_ERR_NONMANIFOLD).  mate is
-//    -1 beforehand.  The same thread then computes the tet's geometry record:
-//    the FP64-bound geometry and the latency-bound probes overlap in the SM's
-//    warp scheduler.  The tets are validated and copied here.
-template <bool DW>
-__global__ void k_face_insert(const int4* __restrict__ tet, int64_t nE, int64_t nC, int lgP, int64_t cap,
-                              int32_t* __restrict__ table, int32_t* __restrict__ mate, int4* __restrict__ tet_copy,
-                              const double* __restrict__ coord, double* __restrict__ geo, unsigned* status) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nE) return;
-  const int4 v = tet[i];
-  tet_copy[i] = v;  // the mesh's own copy of the input
-  if (!valid_tet(v, nC)) {
-    ph_flag(status, PH_ERR_ARG);
-    return;
+// 1. histogram of face keys by bucket
+__global__ void k_face_count(const int4* __restrict__ tet, int64_t nE, int64_t nC, const int32_t* __restrict__ nb,
+                             int64_t nN, int sub, int32_t* __restrict__ cnt, int4* __restrict__ tet_copy,
+                             unsigned* status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < nE) {
+    int4 v = tet[i];
+    tet_copy[i] = v;  // the mesh's own copy of the input
+    if (!valid_tet(v, nC)) { ph_flag(status, PH_ERR_ARG); return; }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) atomicAdd(&cnt[bucket_of(sort3(local_face(v, k)), sub)], 1);
+  } else if (i < nE + nN) {
+    int3 f = neumann_tri(nb, i - nE);
+    if (!valid_tri(f, nC)) { ph_flag(status, PH_ERR_ARG); return; }
+    atomicAdd(&cnt[bucket_of(sort3(f), sub)], 1);
   }
-#pragma unroll 1
-  for (int k = 0; k < 4; ++k) {
-    const int3 key = sort3(local_face(v, k));
-    const int me = (int)(4 * i + k);
-    int64_t h = key_home(key, lgP);
-    int64_t probes = 0;
-    for (;; ++probes) {
-      if (probes == cap) {  // cannot happen: more slots than local faces
-        ph_flag(status, PH_ERR_OVERFLOW);
-        break;
-      }
-      const int o = atomicCAS(table + h, 0, me + 1) - 1;
-      if (o < 0) break;  // claimed
-      if (same_key(sort3(local_face(__ldg(tet + (o >> 2)), o & 3)), key)) {
-        if (atomicCAS(mate + o, -1, me) == -1) mate[me] = o;
-        else ph_flag(status, PH_ERR_NONMANIFOLD);
-        break;
-      }
-      if (++h == cap) h = 0;
-    }
-  }
-  if (DW) tet_geom_dw(coord, v, i, geo, status);
-  else tet_geom(coord, v, i, geo, status);
 }
 
-// 2. Neumann triples (after the tets): each must find its key's claimer, a
-//    local face with no mate, which becomes a Neumann boundary face (mate
-//    -2).  A triple that is no face, lies on an interior face or repeats one
-//    is PH_ERR_ARG.
-__global__ void k_face_neumann(const int32_t* __restrict__ nb, int64_t nN, int64_t nC, const int4* __restrict__ tet,
-                               int lgP, int64_t cap, const int32_t* __restrict__ table, int32_t* __restrict__ mate,
-                               unsigned* status) {
-  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j >= nN) return;
-  const int3 f = neumann_tri(nb, j);
-  if (!valid_tri(f, nC)) {
-    ph_flag(status, PH_ERR_ARG);
-    return;
-  }
-  const int3 key = sort3(f);
-  int64_t h = key_home(key, lgP);
-  for (int64_t probes = 0; probes < cap; ++probes) {
-    const int o = table[h] - 1;
-    if (o < 0) break;  // not a face of the mesh
-    if (same_key(sort3(local_face(tet[o >> 2], o & 3)), key)) {
-      if (atomicCAS(mate + o, -1, -2) != -1) ph_flag(status, PH_ERR_ARG);
-      return;
+// 2. scatter keys into buckets: entry = (v0, v1, v2, slot), slot = 4t+k for
+//    tet faces and 4nE+i for Neumann triples.  cnt counts down to 0.  The
+//    same thread then computes the tet's geometry record: the FP64-bound
+//    geometry and the latency-bound atomics and scattered stores overlap in
+//    the SM's warp scheduler.
+__global__ void k_face_fill(const int4* __restrict__ tet, int64_t nE, int64_t nC, const int32_t* __restrict__ nb,
+                            int64_t nN, int sub, const int32_t* __restrict__ start, int32_t* __restrict__ cnt,
+                            int4* __restrict__ entries, int32_t* __restrict__ mate, const double* __restrict__ coord,
+                            double* __restrict__ geo, bool geo_dw, unsigned* status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (failed(status)) return;
+  if (i < nE) {
+    int4 v = tet[i];
+    if (!valid_tet(v, nC)) return;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      int3 s = sort3(local_face(v, k));
+      const int64_t b = bucket_of(s, sub);
+      int pos = start[b] + atomicSub(&cnt[b], 1) - 1;
+      entries[pos] = make_int4(s.x, s.y, s.z, (int)(4 * i + k));
     }
-    if (++h == cap) h = 0;
+    reinterpret_cast<int4*>(mate)[i] = make_int4(-1, -1, -1, -1);  // no mate yet (boundary)
+    if (geo_dw) tet_geom_dw(coord, v, i, geo, status);
+    else tet_geom(coord, v, i, geo, status);
+  } else if (i < nE + nN) {
+    int3 f = neumann_tri(nb, i - nE);
+    if (!valid_tri(f, nC)) return;
+    int3 s = sort3(f);
+    const int64_t b = bucket_of(s, sub);
+    int pos = start[b] + atomicSub(&cnt[b], 1) - 1;
+    entries[pos] = make_int4(s.x, s.y, s.z, (int)i + 3 * (int)nE);  // slot 4nE + (i - nE)
   }
-  ph_flag(status, PH_ERR_ARG);
+}
+
+// Outcome of one entry's scan: a tet entry records its mate (and its mate's
+// mate) or -2 for a Neumann triple; errors as in k_face_match.
+__device__ __forceinline__ void settle_entry(int4 e, int ntet, int nt, int nn, int tm, int32_t* __restrict__ mate,
+                                             unsigned* status) {
+  if (e.w < ntet) {
+    if (nt + nn >= 2) ph_flag(status, nn > 0 ? PH_ERR_ARG : PH_ERR_NONMANIFOLD);
+    if (nt == 1) {
+      mate[e.w] = tm;
+      mate[tm] = e.w;
+    } else if (nn == 1) {
+      mate[e.w] = -2;
+    }
+  } else {
+    if (nt != 1 || nn != 0) ph_flag(status, PH_ERR_ARG);
+    else mate[tm] = -2;
+  }
+}
+
+// k is an entry of e's bucket (same largest vertex) or the sentinel (-1, ...),
+// which equals no entry
+__device__ __forceinline__ void count_match(int4 k, int4 e, int ntet, int& nt, int& nn, int& tm) {
+  if (k.x == e.x && k.y == e.y) {
+    if (k.w < ntet) { ++nt; tm = k.w; } else { ++nn; }
+  }
+}
+
+// 3. match equal keys inside a bucket.  A tet entry compares itself with the
+//    LATER entries of its bucket only and writes both mates of a pair, so each
+//    pair is found once (a second match marks a face in three tets, or a
+//    Neumann triple on an interior face); Neumann entries (boundary only, few)
+//    scan the whole bucket, themselves included (one Neumann hit taken off),
+//    and must match exactly one tet entry.  Each thread takes two entries, i
+//    and i + half, and scans their buckets in lockstep: two independent chains
+//    of loads in flight per thread.  The kernel issues instructions at close
+//    to the SM's rate, so the loop carries no more than the loads and
+//    compares; the bucket hash keeps the scans short.
+__global__ void k_face_match(const int4* __restrict__ entries, int64_t nent, const int32_t* __restrict__ start,
+                             int sub, int64_t nE, int32_t* __restrict__ mate, unsigned* status) {
+  const int64_t half = (nent + 1) >> 1;
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i0 >= half || failed(status)) return;
+  const int64_t i1 = i0 + half;
+  const bool has1 = i1 < nent;
+  const int ntet = (int)(4 * nE);  // slots are int32
+  const int4 none = make_int4(-1, -1, -1, -1);
+  const int4 e0 = entries[i0];
+  const int4 e1 = has1 ? entries[i1] : none;
+  const int64_t b0 = bucket_of(make_int3(e0.x, e0.y, e0.z), sub);
+  const int64_t b1 = has1 ? bucket_of(make_int3(e1.x, e1.y, e1.z), sub) : 0;
+  const int end0 = start[b0 + 1], end1 = has1 ? start[b1 + 1] : 0;
+  // tet entries scan the later entries of their bucket, Neumann entries all of it
+  const bool nm0 = e0.w >= ntet, nm1 = has1 && e1.w >= ntet;
+  int j0 = nm0 ? start[b0] : (int)i0 + 1;
+  int j1 = has1 ? (nm1 ? start[b1] : (int)i1 + 1) : 0;
+  int nt0 = 0, nn0 = nm0 ? -1 : 0, tm0 = -1, nt1 = 0, nn1 = nm1 ? -1 : 0, tm1 = -1;
+  while (j0 < end0 || j1 < end1) {
+    const int4 k0 = j0 < end0 ? entries[j0] : none;
+    const int4 k1 = j1 < end1 ? entries[j1] : none;
+    count_match(k0, e0, ntet, nt0, nn0, tm0);
+    count_match(k1, e1, ntet, nt1, nn1, tm1);
+    ++j0;
+    ++j1;
+  }
+  settle_entry(e0, ntet, nt0, nn0, tm0, mate, status);
+  if (has1) settle_entry(e1, ntet, nt1, nn1, tm1, mate, status);
 }
 
 // 4. face bases: an exclusive scan of the number of first occurrences per tet,
@@ -595,11 +637,12 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
   const int64_t nFmax = 4 * nE + nN, nnzmax = nFmax + 12 * nE;
   if (nnzmax >= ((int64_t)1 << 31) - 1 || nC >= ((int64_t)1 << 31) - 1) return PH_ERR_OVERFLOW;
   ph_status st = PH_OK;  // everything runs in order on the caller's stream s
-  // face-key table: nC << lgP slots, more than the 4 nE local faces (about
-  // three in ten hold a face on a closed mesh)
-  int lgP = 0;
-  while (nE > 0 && nC > 0 && (nC << lgP) <= 4 * nE) ++lgP;
-  const int64_t cap = (nE > 0 && nC > 0) ? (nC << lgP) : 0;
+  // face-key buckets: 4 per largest vertex while the bucket ids stay below 2^31
+  // (finer buckets shorten the match scans but cost more in the scattered
+  // fill and the bucket scan than they save)
+  const int sub = nC < ((int64_t)1 << 28) ? 2 : 0;
+  const int64_t nb = (nC << sub) + 1;
+  const int64_t nent = nFmax;
   const unsigned gF = grid_for(nFmax + 1);
   ph_mesh* m = new ph_mesh();
   memset(m, 0, sizeof *m);
@@ -616,14 +659,15 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
   const size_t o_farea = mc.take<double>(nFmax), o_rowptr = mc.take<int32_t>(nFmax + 1);
   const size_t o_colind = mc.take<int32_t>(nnzmax), o_rowdiag = mc.take<int32_t>(nFmax);
   // scratch: zeroed part first
-  const size_t o_tot = sc.take<int64_t>(3), o_table = sc.take<int32_t>(cap);
+  const size_t o_tot = sc.take<int64_t>(3), o_cnt = sc.take<int32_t>(nb);
+  const size_t o_s1 = sc.take<unsigned long long>(scan_state_words(nb));
   const size_t o_s2 = sc.take<unsigned long long>(scan_state_words(nE + 1));
   const size_t o_s3 = sc.take<unsigned long long>(scan_state_words(nFmax + 1));
   const size_t o_s4 = sc.take<unsigned long long>(scan_state_words(nFmax + 1));
   const size_t o_rowlen = sc.take<int32_t>(nN > 0 || nE == 0 ? nFmax + 1 : 0);  // else written by k_face_emit
   const size_t o_flag = sc.take<int32_t>(nN > 0 ? nFmax + 1 : 0);
   const size_t zero_bytes = sc.bytes;
-  const size_t o_mate = sc.take<int32_t>(4 * nE);
+  const size_t o_start = sc.take<int32_t>(nb), o_entries = sc.take<int4>(nent), o_mate = sc.take<int32_t>(4 * nE);
   const size_t o_newc = sc.take<int32_t>(nE + 1);
   const size_t o_rowlen2 = sc.take<int32_t>(nN > 0 || nE == 0 ? 0 : nFmax + 1);
   void* scratch = nullptr;
@@ -653,30 +697,41 @@ static ph_status mesh_build(const double* coord, int64_t nC, const int32_t* tet,
   }
   {
   int64_t* d_tot = Carve::at<int64_t>(scratch, o_tot);  // [0] nF, [1] L, [2] nnz
-  int32_t* table = Carve::at<int32_t>(scratch, o_table);
+  int32_t* cnt = Carve::at<int32_t>(scratch, o_cnt);
   int32_t* newc = Carve::at<int32_t>(scratch, o_newc);
+  int32_t* start = Carve::at<int32_t>(scratch, o_start);
+  int4* entries = Carve::at<int4>(scratch, o_entries);
   int32_t* mate = Carve::at<int32_t>(scratch, o_mate);
   int32_t* flag = nN > 0 ? Carve::at<int32_t>(scratch, o_flag) : nullptr;
   int32_t* rowlen = Carve::at<int32_t>(scratch, (nN > 0 || nE == 0) ? o_rowlen : o_rowlen2);
+  unsigned long long* st1 = Carve::at<unsigned long long>(scratch, o_s1);
   unsigned long long* st2 = Carve::at<unsigned long long>(scratch, o_s2);
   unsigned long long* st3 = Carve::at<unsigned long long>(scratch, o_s3);
   unsigned long long* st4 = Carve::at<unsigned long long>(scratch, o_s4);
   PH_CU(cudaMemsetAsync(scratch, 0, zero_bytes, s), "memset");
-  if (nE > 0) PH_CU(cudaMemsetAsync(mate, 0xFF, sizeof(int32_t) * 4 * nE, s), "memset");  // -1: no mate yet
   PH_CU(cudaMemsetAsync(m->status, 0, sizeof(unsigned), s), "memset");
   if (nC > 0) PH_CU(cudaMemcpyAsync(m->coord, coord, sizeof(double) * 3 * nC, cudaMemcpyDeviceToDevice, s), "copy");
 
-  // --- faces: key table and mates, then the numbering -----------------------
-  if (nE > 0) {
-    KernelTimer kt("k_face_insert", s, 2);
-    (dw ? k_face_insert<true> : k_face_insert<false>)<<<grid_for(nE), kThreads, 0, s>>>(
-        reinterpret_cast<const int4*>(tet), nE, nC, lgP, cap, table, mate, m->tet, m->coord, m->geo, m->status);
-    PH_CU(launched(), "k_face_insert");
+  // --- faces: bucket the keys, match them, number the faces ----------------
+  if (nent > 0) {
+    KernelTimer kt("k_face_count", s, 2);
+    k_face_count<<<grid_for(nE + nN), kThreads, 0, s>>>(reinterpret_cast<const int4*>(tet), nE, nC, neumann, nN,
+                                                        sub, cnt, m->tet, m->status);
+    PH_CU(launched(), "k_face_count");
   }
-  if (nN > 0) {  // after the tets (with no tets, cap = 0: every triple is no face)
-    k_face_neumann<<<grid_for(nN), kThreads, 0, s>>>(neumann, nN, nC, reinterpret_cast<const int4*>(tet), lgP, cap,
-                                                     table, mate, m->status);
-    PH_CU(launched(), "k_face_neumann");
+  PH_TRY(exclusive_scan(cnt, start, nb, d_tot, s, m->status, nullptr, 0, st1));
+  if (nent > 0) {
+    {
+      KernelTimer kt("k_face_fill", s, 2);
+      k_face_fill<<<grid_for(nE + nN), kThreads, 0, s>>>(m->tet, nE, nC, neumann, nN, sub, start, cnt, entries,
+                                                         mate, m->coord, m->geo, dw, m->status);
+      PH_CU(launched(), "k_face_fill");
+    }
+    {
+      KernelTimer kt("k_face_match", s, 2);
+      k_face_match<<<grid_for((nent + 1) / 2), kThreads, 0, s>>>(entries, nent, start, sub, nE, mate, m->status);
+      PH_CU(launched(), "k_face_match");
+    }
   }
   // face bases: the scan counts each tet's first occurrences from the mates
   PH_TRY(exclusive_scan(nullptr, newc, nE + 1, d_tot, s, m->status, nullptr, 0, st2,

@@ -71,7 +71,7 @@ def test_allocation_failure_returns_nomem_without_leak(ph):
 
 
 def test_scan_lookback_timeout(ph):
-    coord, tet = kuhn(16)  # 24,576 tets: the scan over the tets spans 7 tiles of 4096
+    coord, tet = kuhn(16)  # 4913 vertices: the bucket scan spans 5 tiles of 4096
     c_d, t_d = cu(coord), cu(tet)
     ph.ph_test_scan_withhold(True)
     try:

@@ -129,9 +129,8 @@ CASES = ["listing1", "listing1_mixed", "sin_kuhn", "kuhn_m2_k1", "shuffled", "mi
 
 def renumber_by_degree(coord, tet, lists=()):
     """Vertices renumbered by ascending number of incident tets, so that the
-    busiest vertices are the largest ids of most of their faces: up to 108
-    face keys share one largest vertex (tet and Neumann keys mixed), so their
-    probes run far past their home slots."""
+    busiest vertices are the largest ids of most of their faces: face-key
+    buckets of up to 108 entries (tet and Neumann keys mixed)."""
     deg = np.bincount(tet.ravel(), minlength=coord.shape[0])
     order = np.argsort(deg, kind="stable")
     inv = np.empty_like(order)
