@@ -145,10 +145,11 @@ def check_all_values(p, g, what):
         e = np.abs(g[k] - o["U"]).max(axis=1)
         t = int(np.argmax(e / scale))
         over[k] = int(np.count_nonzero(e > bar))
+        big = e > VAL_RTOL * scale  # the cancelling elements
+        ulps = float((e[big] / (EPS64 * terms[big])).max()) if big.any() else 0.0
         print(f"{p.name} {what} {k}: worst {e[t] / scale[t]:.3g} of max|U| at element {t}, whose terms are "
-              f"{terms[t] / scale[t]:.3g} x max|U|; worst {float((e / (EPS64 * terms)).max()):.3g} ulp of the "
-              f"terms; {int(np.count_nonzero(e > 1e-12 * scale))} of {e.size} elements above 1e-12 max|U|, "
-              f"{over[k]} above the bar")
+              f"{terms[t] / scale[t]:.3g} x max|U|; {int(big.sum())} of {e.size} elements above 1e-12 max|U|, "
+              f"at most {ulps:.3g} ulp of their terms; {over[k]} above the bar")
     print(f"{p.name} {what}: {o['values'].size} H values, worst relative error {ratio:.3g} ({bad} above "
           f"{VAL_RTOL:g}); rhs worst {rerr:.3g} of the addends' magnitudes")
     assert bad == 0, (bad, ratio)
