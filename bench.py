@@ -339,7 +339,7 @@ def gpu_arm(args, rank, world, local_rank):
             m.assemble(a_d, p.c, f_d, values=values, rhs=rhs, factor=factor, variant="dw")
             if ev is not None:
                 ev[3].record(stream)
-            m.recover_factored(factor, p.c, f_d, lam_d, u=u)
+            m.recover_factored(factor, p.c, f_d, lam_d, u=u, variant="dw")
             if ev is not None:
                 ev[1].record(stream)
             m.close()
@@ -350,6 +350,7 @@ def gpu_arm(args, rank, world, local_rank):
         torch.cuda.synchronize()
         evd = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
         ph.ph_kernel_time("k_assemble_dw", reset=True)
+        ph.ph_kernel_time("k_recover_factored_dw", reset=True)
         ph.ph_timing_enable(True)
         for i in range(args.steps):
             step_dw(evd[i])
@@ -357,6 +358,7 @@ def gpu_arm(args, rank, world, local_rank):
         torch.cuda.synchronize()
         ph.ph_timing_enable(False)
         ms, n = ph.ph_kernel_time("k_assemble_dw", reset=True)
+        rms, rn = ph.ph_kernel_time("k_recover_factored_dw", reset=True)
         # the double-word mesh build's kernels, in a short loop of their own
         for name in BUILD_KERNELS:
             ph.ph_kernel_time(name, reset=True)
@@ -374,8 +376,9 @@ def gpu_arm(args, rank, world, local_rank):
                    "mesh_build_kernels_ms": build_dw,
                    "phases_ms": {"mesh_create_dw": float(np.mean([e[0].elapsed_time(e[2]) for e in evd])),
                                  "assemble_dw": float(np.mean([e[2].elapsed_time(e[3]) for e in evd])),
-                                 "recover": float(np.mean([e[3].elapsed_time(e[1]) for e in evd]))},
-                   "k_assemble_dw_ms": ms / n if n else float("nan")}
+                                 "recover_dw": float(np.mean([e[3].elapsed_time(e[1]) for e in evd]))},
+                   "k_assemble_dw_ms": ms / n if n else float("nan"),
+                   "k_recover_factored_dw_ms": rms / rn if rn else float("nan")}
     # the FP64 pipe's throughput on this GPU, measured now, under the same
     # clock sampling as the timed steps: best of 3 probe launches
     ph.ph_fp64_peak(FP64_PEAK_ITERS)
@@ -550,16 +553,18 @@ def variant_report(v, nE, nC, nF, world, fp64_peak_gops, hbm_peak, f64_step_ms, 
     prof = profile_figures("k_assemble_dw")
     bpt = assemble_bytes_per_tet(nE, nC, nF)
     out = {
-        "what": "ph_mesh_create_dw + ph_assemble_dw + ph_recover_factored: the element geometry (G_e, G_e T0^-1), "
-                "the face areas and the condensation kernel (the 3x3 algebra of A^-1) in double-word arithmetic "
-                "(float pairs, ~48 bits) on the FP32 pipe; edge vectors, |det E|, the leading term d d'/(c|T|) "
-                "and every sum of H and rhs in fp64; flat or reaction-dominated elements take the fp64 kernel; "
-                "tested against the oracle at the fp64 path's tolerances (1e-12)",
+        "what": "ph_mesh_create_dw + ph_assemble_dw + ph_recover_factored_dw: the element geometry (G_e, "
+                "G_e T0^-1), the condensation kernel (the 3x3 algebra of A^-1) and the recovery's product "
+                "(Qf/9) z' in double-word arithmetic (float pairs, ~48 bits) on the FP32 pipe; edge vectors, "
+                "|det E|, face areas, the leading term d d'/(c|T|), every sum of H and rhs and the recovery's "
+                "z' terms in fp64; flat or reaction-dominated elements take the fp64 kernel; tested against the "
+                "oracle at the fp64 path's bars",
         "dtype": "f64 + f32x2 (double-word) geometry and condensation kernel",
         "value": whole_job_rate(nE, world, v["step_ms"]), "unit": UNIT, "ms_per_step": v["step_ms"],
         "phases_ms": v["phases_ms"], "mesh_build_kernels_ms": v["mesh_build_kernels_ms"],
         "speedup_step_vs_f64": f64_step_ms / v["step_ms"],
         "k_assemble_dw_ms": v["k_assemble_dw_ms"], "speedup_kernel_vs_f64": f64_k_asm_ms / v["k_assemble_dw_ms"],
+        "k_recover_factored_dw_ms": v["k_recover_factored_dw_ms"],
         "roofline_hbm": {"achieved": bpt * nE / k_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                          "frac": bpt * nE / k_s / 1e9 / hbm_peak, "bytes_per_tet": bpt,
                          "traffic": prof["dram_bytes_per_tet"] * nE if "dram_bytes_per_tet" in prof else None},
@@ -835,8 +840,9 @@ def profile_pcg(iters):
 
 def profile_kernels(workload, reps, variant="f64"):
     """Profiler target for the element kernels: on the given workload, `reps`
-    rounds of assembly with the element factor (ph_assemble, or
-    ph_assemble_dw for variant "dw"), recovery from a seeded Lambda, the
+    rounds of assembly with the element factor and recovery from a seeded
+    Lambda (ph_assemble and ph_recover_factored, or their double-word
+    versions for variant "dw"), the
     misfit, the adjoint right-hand side and the adjoint gradient from a seeded
     q (no solves, so few launches)."""
     import torch
@@ -857,7 +863,7 @@ def profile_kernels(workload, reps, variant="f64"):
     u_obs = torch.as_tensor(rng.standard_normal((mesh.nE, 4)), device=dev)
     for _ in range(reps):
         values, rhs, factor = mesh.assemble(a, p.c, f, factor=True, variant=variant)
-        u = mesh.recover_factored(factor, p.c, f, lam)
+        u = mesh.recover_factored(factor, p.c, f, lam, variant=variant)
         mesh.misfit(u, u_obs)
         mesh.adjoint_rhs(factor, p.c, u, u_obs)
         if variant == "f64":  # the gradient reads the fp64 geometry record

@@ -132,7 +132,7 @@ ph_status ph_mesh_create_batch(int32_t n, const double* const* coord, const int6
  * pairs of floats, computed in double-word arithmetic on the FP32 pipe from
  * the fp64 edge vectors (|det E|, 1/|det E| and the face areas |F| stay the
  * fp64 values: the leading terms of H and of the recovery need their last
- * bits).  Such a mesh works with ph_assemble_dw, ph_recover_factored, ph_misfit,
+ * bits).  Such a mesh works with ph_assemble_dw, ph_recover_factored(_dw), ph_misfit,
  * ph_adjoint_rhs and every connectivity, CSR and solver entry point; the
  * entry points that read the fp64 record (ph_assemble, ph_recover,
  * ph_adjoint_grad, ph_batch_create) return PH_ERR_ARG for it.
@@ -233,6 +233,18 @@ ph_status ph_recover(const ph_mesh* mesh, const double* a, double c, const doubl
  */
 ph_status ph_recover_factored(const ph_mesh* mesh, const double* factor, double c, const double* f_face,
                               const double* gN_face, const double* lambda, double* u, void* stream);
+
+/*
+ * ph_recover_factored with the product (Qf/9) z' of Algorithm 1's second
+ * loop in double-word arithmetic (float pairs, ~48 bits) on the FP32 pipe:
+ * 18 FP64 operations per element instead of 34.  z' = |T|/4 f + d Lambda,
+ * its sum and U = z'sum/(c|T|) - 3 (Qf/9) z' stay fp64, so the result is
+ * ph_recover_factored's to the rounding of those terms.  Works on meshes from
+ * ph_mesh_create and ph_mesh_create_dw; arguments, errors and the one kernel
+ * as ph_recover_factored.
+ */
+ph_status ph_recover_factored_dw(const ph_mesh* mesh, const double* factor, double c, const double* f_face,
+                                 const double* gN_face, const double* lambda, double* u, void* stream);
 
 /*
  * Solve H x = b for a symmetric positive definite CSR matrix (rowptr [n+1],

@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "PH_OK", 1: "PH_ERR_ARG", 2: "PH_ERR_DEGENERATE", 3: "PH_ERR_
 # Every symbol declared in include/ph.h.
 EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces", "ph_csr_pattern", "ph_assemble",
            "ph_recover", "ph_solve_pcg", "ph_mesh_check", "ph_status_string", "ph_last_error_message",
-           "ph_launch_count", "ph_solve_pcg_noalloc", "ph_recover_factored", "ph_spmv", "ph_misfit",
+           "ph_launch_count", "ph_solve_pcg_noalloc", "ph_recover_factored", "ph_recover_factored_dw", "ph_spmv",
+           "ph_misfit",
            "ph_adjoint_rhs", "ph_adjoint_grad", "ph_batch_create", "ph_batch_destroy", "ph_batch_bind",
            "ph_batch_assemble", "ph_batch_autotune", "ph_batch_set_config", "ph_batch_get_config",
            "ph_batch_graph_launch", "ph_refine", "ph_refined_info", "ph_refined_copy", "ph_refined_destroy", "ph_rcp", "ph_half_sqrt", "ph_timing_enable",
@@ -78,6 +79,7 @@ def load(path: str | None = None):
         "ph_assemble": [P, P, D, P, P, P, P, P, P, P],
         "ph_assemble_dw": [P, P, D, P, P, P, P, P, P, P],
         "ph_recover_factored": [P, P, D, P, P, P, P, P],
+        "ph_recover_factored_dw": [P, P, D, P, P, P, P, P],
         "ph_recover": [P, P, D, P, P, P, P, P],
         "ph_solve_pcg": [I64, P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P],
         "ph_solve_pcg_noalloc": [I64, P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P],
@@ -382,15 +384,20 @@ class Mesh:
                                  _stream(stream)), "ph_recover")
         return u
 
-    def recover_factored(self, factor, c, f_face, lam, gN_face=None, u=None, stream=None):
+    def recover_factored(self, factor, c, f_face, lam, gN_face=None, u=None, stream=None, variant="f64"):
+        """U from the element factor of assemble(); variant "dw" computes the
+        factor's product in double-word arithmetic (ph_recover_factored_dw)."""
+        if variant not in ("f64", "dw"):
+            raise ValueError("variant: 'f64' or 'dw'")
+        name = "ph_recover_factored" if variant == "f64" else "ph_recover_factored_dw"
         _need(factor, torch.float64, 10 * self.nE, "factor")
         _need(f_face, torch.float64, self.nF, "f_face")
         _need(lam, torch.float64, self.L, "lambda")
         if gN_face is not None:
             _need(gN_face, torch.float64, self.nF, "gN_face")
         u = self._empty((self.nE, 4), torch.float64) if u is None else _need(u, torch.float64, 4 * self.nE, "u")
-        _check(load().ph_recover_factored(self._h, _ptr(factor), float(c), _ptr(f_face), _ptr(gN_face), _ptr(lam),
-                                          _ptr(u), _stream(stream)), "ph_recover_factored")
+        _check(getattr(load(), name)(self._h, _ptr(factor), float(c), _ptr(f_face), _ptr(gN_face), _ptr(lam),
+                                     _ptr(u), _stream(stream)), name)
         return u
 
     def misfit(self, u, u_obs, stream=None):

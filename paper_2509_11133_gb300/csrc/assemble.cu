@@ -179,6 +179,21 @@ extern "C" ph_status ph_assemble(const ph_mesh* m, const double* a, double c, co
   return assemble<false>(m, a, c, f_face, uD_face, gN_face, values, rhs, factor, stream);
 }
 
+template <bool GN>
+__global__ void __launch_bounds__(128) k_recover_factored_dw(int64_t nE, const double* __restrict__ geo,
+                                                             const int4* __restrict__ tface,
+                                                             const int4* __restrict__ tmult,
+                                                             const double* __restrict__ face_area,
+                                                             const double* __restrict__ factor, double six_over_c,
+                                                             const double* __restrict__ f_face,
+                                                             const double* __restrict__ gN,
+                                                             const double* __restrict__ lambda,
+                                                             double* __restrict__ u) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nE) return;
+  recover_element_factored_dw<GN>(t, geo, tface, tmult, face_area, factor, six_over_c, f_face, gN, lambda, u);
+}
+
 extern "C" ph_status ph_assemble_dw(const ph_mesh* m, const double* a, double c, const double* f_face,
                                     const double* uD_face, const double* gN_face, double* values, double* rhs,
                                     double* factor, void* stream) {
@@ -224,4 +239,24 @@ extern "C" ph_status ph_recover_factored(const ph_mesh* m, const double* factor,
   const cudaError_t e = launched();
   kt.stop();
   return cuda_status(e, "k_recover_factored");
+}
+
+extern "C" ph_status ph_recover_factored_dw(const ph_mesh* m, const double* factor, double c, const double* f_face,
+                                            const double* gN_face, const double* lambda, double* u, void* stream) {
+  if (!m || !finite_pos(c)) return PH_ERR_ARG;
+  if (m->nE > 0 && (!factor || !f_face || !u || (m->L > 0 && !lambda))) return PH_ERR_ARG;
+  if (m->nE == 0) return PH_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double six_over_c = 6.0 / c;
+  const unsigned grid = grid_for(m->nE, 128);
+  KernelTimer kt("k_recover_factored_dw", s);
+  if (gN_face != nullptr && m->nFn > 0)
+    k_recover_factored_dw<true><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->face_area, factor,
+                                                     six_over_c, f_face, gN_face, lambda, u);
+  else
+    k_recover_factored_dw<false><<<grid, 128, 0, s>>>(m->nE, m->geo, m->tface, m->tmult, m->face_area, factor,
+                                                      six_over_c, f_face, gN_face, lambda, u);
+  const cudaError_t e = launched();
+  kt.stop();
+  return cuda_status(e, "k_recover_factored_dw");
 }

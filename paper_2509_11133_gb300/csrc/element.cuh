@@ -423,4 +423,64 @@ __device__ __forceinline__ void recover_element_factored(int64_t t, const double
   store_u(u, t, U);
 }
 
+// The same recovery with the product (Qf/9) z' in double-word arithmetic on
+// the FP32 pipe (dw.cuh): the factor and z' become float pairs scaled by the
+// element's largest binade of each, each row sum returns to fp64 exactly
+// scaled.  z', its sum and the final combination stay fp64: they are the
+// terms whose rounding bounds the result when a Lambda that is not a
+// solution makes them cancel, and the pairs' ~2^-47 lands on the smaller
+// (Qf z')/3 (a factor c h^2/a below them).  18 FP64 operations per element
+// instead of 34.  Elements whose binades leave the pairs' range take the fp64
+// product.
+template <bool GN>
+__device__ __forceinline__ void recover_element_factored_dw(int64_t t, const double* __restrict__ geo,
+                                                            const int4* __restrict__ tface,
+                                                            const int4* __restrict__ tmult,
+                                                            const double* __restrict__ face_area,
+                                                            const double* __restrict__ factor, double six_over_c,
+                                                            const double* __restrict__ f_face,
+                                                            const double* __restrict__ gN,
+                                                            const double* __restrict__ lambda,
+                                                            double* __restrict__ u) {
+  using namespace dw;
+  const double2 dr = __ldg(reinterpret_cast<const double2*>(geo + PH_GEO_STRIDE * t) + 7);  // (t22, |det|)
+  const double rdet = __ldg(geo + PH_GEO_STRIDE * t + 16);
+  double z[4];
+  recovery_load<GN>(dr.y * (1.0 / 24.0), __ldg(tface + t), __ldg(tmult + t), face_area, f_face, gN, lambda, z);
+  const double2* fp = reinterpret_cast<const double2*>(factor + 10 * t);
+  const double2 q0 = __ldg(fp), q1 = __ldg(fp + 1), q2 = __ldg(fp + 2), q3 = __ldg(fp + 3), q4 = __ldg(fp + 4);
+  const double Q[10] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y, q3.x, q3.y, q4.x, q4.y};
+  const double icT = rdet * six_over_c;
+  const double zs = icT * ((z[0] + z[1]) + (z[2] + z[3]));
+  int kq = -1023, kz = -1023;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) kq = max(kq, exponent(Q[i]));
+#pragma unroll
+  for (int m = 0; m < 4; ++m) kz = max(kz, exponent(z[m]));
+  double U[4];
+  if (kq > -900 && kq < 900 && kz > -900 && kz < 900 && kq + kz > -1000 && kq + kz < 1000) {
+    f2 qd[10], zd[4];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) qd[i] = from_double(Q[i], -kq);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) zd[m] = from_double(z[m], -kz);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      f2 v = mul(qd[ut(k, 0)], zd[0]);
+#pragma unroll
+      for (int m = 1; m < 4; ++m) v = add(v, mul(qd[ut(k, m)], zd[m]));
+      U[k] = fma(-3.0, to_double(v, kq + kz), zs);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double e = 0.0;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) e = fma(Q[ut(k, m)], z[m], e);
+      U[k] = fma(-3.0, e, zs);
+    }
+  }
+  store_u(u, t, U);
+}
+
 }  // namespace ph_elem

@@ -245,3 +245,32 @@ def test_dw_mesh_refuses_fp64_record_entry_points(ph):
             call()
         assert e.value.name == "PH_ERR_ARG"
     m.close()
+
+
+@pytest.mark.parametrize("name", ["sin_kuhn", "mixed_l2", "lognormal_small", "jitter_checker_small", "shuffled"])
+def test_dw_recovery_parity(ph, name):
+    """ph_recover_factored_dw, from the fp64 factor and from the double-word
+    factor, against the oracle's recovery with a random Lambda: within 1e-12
+    of each element's largest |U| plus 8 ulp of the magnitude of the terms the
+    recovery sums (z' and its sum stay fp64; the pairs carry the smaller
+    (Qf z')/3); the fp64 path's factor recovery printed beside it."""
+    from tests.test_gpu_fullsize import EPS64, U_TERM_ULPS, recovery_terms
+    p = make_case(name)
+    g = run_both(ph, p)
+    fc = oracle.faces(p.tet, p.nC, p.neumann)
+    fm, L = oracle.multipliers(fc["face_kind"])
+    lam = np.random.default_rng(2).standard_normal(L)
+    fo, _, gNo = oracle_face_data(p, fc)
+    Uo = oracle.recover(p.coord, p.tet, fc, fm, p.a, p.c, fo, lam, gNo)
+    gN = None if g["gN"] is None else cu(g["gN"], torch.float64)
+    args = (p.c, cu(g["f"], torch.float64), cu(lam, torch.float64), gN)
+    scale = np.abs(Uo).max(axis=1)
+    terms = recovery_terms(p, {"fc": fc, "f": fo, "gN": gNo, "lam": lam, "csr": {"face_mult": fm}})
+    bar = 1e-12 * scale + U_TERM_ULPS * EPS64 * terms
+    for fac in ("f64", "dw"):
+        for variant in ("f64", "dw"):
+            u = host(g["mesh"].recover_factored(g[fac]["factor_d"], *args, variant=variant))
+            e = np.abs(u - Uo).max(axis=1)
+            print(f"{name}: factor {fac}, recovery {variant}: worst {float((e / scale).max()):.3g} of max|U|")
+            assert np.all(e <= bar), (fac, variant)
+    g["mesh"].close()

@@ -71,7 +71,8 @@ def oracle_data(p):
 
 def run_full(ph, p, geometry="f64", variant="f64"):
     """The full-size path on the GPU: mesh build, assembly with the element
-    factor, recovery with and (fp64 record) without the factor."""
+    factor, recovery with and (fp64 record) without the factor; variant "dw"
+    assembles with ph_assemble_dw and recovers with ph_recover_factored_dw."""
     dev = torch.device("cuda")
     mesh = ph.Mesh(torch.as_tensor(p.coord, device=dev), torch.as_tensor(p.tet, device=dev), geometry=geometry)
     fc = {k: _host(v) for k, v in mesh.faces().items()}
@@ -82,7 +83,7 @@ def run_full(ph, p, geometry="f64", variant="f64"):
     lam = np.random.default_rng(LAM_SEED).standard_normal(mesh.L)
     lam_d = torch.as_tensor(lam, device=dev)
     u = mesh.recover(a_d, p.c, f_d, lam_d) if geometry == "f64" else None
-    uf = mesh.recover_factored(factor, p.c, f_d, lam_d)
+    uf = mesh.recover_factored(factor, p.c, f_d, lam_d, variant=variant)
     mesh.check()
     out = dict(info=dict(mesh.info), fc=fc, rowptr=_host(rowptr), colind=_host(colind), values=_host(values),
                rhs=_host(rhs), U=None if u is None else _host(u), U_factored=_host(uf))
@@ -102,14 +103,20 @@ def check_connectivity(p, g):
 
 def recovery_terms(p, o):
     """Per element, the magnitude of the terms the recovery sums,
-    (1/(c|T|)) sum_m (|T|/4 |f_m| + |F_m| |Lambda_m|): the scale of the
-    rounding in U = z'sum/(c|T|) - 3 (Qf/9) z' (numpy, from the mesh)."""
+    (1/(c|T|)) sum_m (|T|/4 |f_m| + |F_m| |Lambda_m or g_N,m|): the scale of
+    the rounding in U = z'sum/(c|T|) - 3 (Qf/9) z' (numpy, from the mesh; o
+    holds the oracle's faces, face data, multipliers and Lambda, and g_N when
+    the mesh has Neumann faces)."""
     P = p.coord[p.tet]
     vol = np.abs(np.linalg.det(P[:, 1:] - P[:, :1])) / 6.0
     x = p.coord[o["fc"]["face_vtx"]]
     area = 0.5 * np.linalg.norm(np.cross(x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]), axis=1)
     F = o["fc"]["tet_face"] & 0x7FFFFFFF
-    z = vol[:, None] / 4 * np.abs(o["f"][F]) + area[F] * np.abs(o["lam"][o["csr"]["face_mult"][F]])
+    l = o["csr"]["face_mult"][F]
+    side = np.abs(o["lam"][np.maximum(l, 0)])
+    if o.get("gN") is not None:
+        side = np.where(l >= 0, side, np.abs(o["gN"][F]))
+    z = vol[:, None] / 4 * np.abs(o["f"][F]) + area[F] * side
     return z.sum(axis=1) / (p.c * vol)
 
 
@@ -248,8 +255,8 @@ def test_lognormal_3m_properties(lognormal):
 
 def test_lognormal_3m_double_word_variant(ph, lognormal):
     """ph_assemble_dw on the fp64 record of the 3.36M-tet mesh: every H value,
-    rhs entry and value recovered from its element factor, at the fp64
-    path's bars."""
+    rhs entry and value recovered from its element factor by
+    ph_recover_factored_dw, at the fp64 path's bars."""
     p, _ = lognormal
     g = run_full(ph, p, "f64", "dw")
     g["U"] = None
@@ -276,7 +283,7 @@ def test_jitter_checker_18m_properties(jitter):
 
 
 def test_jitter_checker_18m_double_word_mesh(ph, jitter):
-    """ph_mesh_create_dw + ph_assemble_dw + ph_recover_factored on the
+    """ph_mesh_create_dw + ph_assemble_dw + ph_recover_factored_dw on the
     17.9M-tet jittered mesh, the variant bench.py times: connectivity
     bit-exact, every H value, rhs entry and recovered value at the fp64
     path's bars."""
