@@ -669,12 +669,6 @@ def batched_section(ph, dev, steps, warmup):
     n0 = ph.ph_launch_count()
     plain_ms = timed(plain)
     launches_plain = (ph.ph_launch_count() - n0) / (steps + warmup)
-    # the double-word variant of the same batch (ph_assemble_dw and
-    # ph_recover_factored_dw element code), autotuned on its own
-    batch.set_variant("dw")
-    tune_dw_ms = batch.autotune(reps=2)
-    cfg_dw = dict(batch.get_config(), best_ms=tune_dw_ms)
-    graph_dw_ms = timed(batch.graph_launch)
     batch.close()
     for p in probs:
         p["mesh"].close()
@@ -686,8 +680,6 @@ def batched_section(ph, dev, steps, warmup):
         "plain_sequential_ms": plain_ms, "plain_sequential_tets_per_s": total / (plain_ms * 1e-3),
         "speedup_vs_sequential": plain_ms / graph_ms, "autotuned": cfg,
         "launches_per_batch": {"graph": launches_graph, "sequential": launches_plain},
-        "double_word_variant": {"batched_graph_ms": graph_dw_ms, "batched_tets_per_s": total / (graph_dw_ms * 1e-3),
-                                "speedup_vs_fp64_batch": graph_ms / graph_dw_ms, "autotuned": cfg_dw},
     }
 
 

@@ -342,15 +342,6 @@ ph_status ph_batch_graph_launch(ph_batch* batch, void* stream);
  * rebuilt on its next launch when the recovery is added or removed.
  */
 ph_status ph_batch_bind_recovery(ph_batch* batch, const double* const* lambda, double* const* u, void* stream);
-/*
- * ph_batch_set_variant: 0 (the default) runs the fp64 element code; 1 the
- * double-word variant, each problem's values, rhs and factor then
- * bit-identical to ph_assemble_dw on its mesh and its u to
- * ph_recover_factored_dw (blocks of at most 128 threads).  The graph is
- * rebuilt on its next launch when the variant changes.  PH_ERR_ARG for any
- * other value.
- */
-ph_status ph_batch_set_variant(ph_batch* batch, int32_t variant);
 
 /*
  * Uniform refinement on the device (Section 3.4, Listing RedRefine): every

@@ -37,7 +37,7 @@ EXPORTS = ("ph_mesh_create", "ph_mesh_destroy", "ph_mesh_info", "ph_mesh_faces",
            "ph_kernel_time", "ph_assemble_host", "ph_schwarz_create", "ph_schwarz_destroy",
            "ph_solve_pcg_schwarz", "ph_fp64_peak", "ph_test_fail_alloc", "ph_test_scan_withhold",
            "ph_pool_in_use", "ph_solve_refined", "ph_mesh_create_batch", "ph_host_mesh_query",
-           "ph_assemble_dw", "ph_batch_bind_recovery", "ph_mesh_create_dw", "ph_batch_set_variant")
+           "ph_assemble_dw", "ph_batch_bind_recovery", "ph_mesh_create_dw")
 
 
 class PHError(RuntimeError):
@@ -97,7 +97,6 @@ def load(path: str | None = None):
         "ph_batch_get_config": [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)],
         "ph_batch_graph_launch": [P, P],
         "ph_batch_bind_recovery": [P, P, P, P],
-        "ph_batch_set_variant": [P, I32],
         "ph_refine": [P, I64, P, I64, P, I64, P, ctypes.POINTER(P)],
         "ph_refined_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)],
         "ph_refined_copy": [P, P, P, P, P],
@@ -629,13 +628,6 @@ class Batch:
         _check(load().ph_batch_bind_recovery(self._h, _ptr_array(lam), _ptr_array(u), _stream(stream)),
                "ph_batch_bind_recovery")
         self._recovery = (lam, u)
-
-    def set_variant(self, variant):
-        """"f64" (default) or "dw": the double-word element code of
-        ph_assemble_dw and ph_recover_factored_dw."""
-        if variant not in ("f64", "dw"):
-            raise ValueError("variant: 'f64' or 'dw'")
-        _check(load().ph_batch_set_variant(self._h, 0 if variant == "f64" else 1), "ph_batch_set_variant")
 
     def assemble(self, stream=None):
         _check(load().ph_batch_assemble(self._h, _stream(stream)), "ph_batch_assemble")

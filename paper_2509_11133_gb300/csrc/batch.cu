@@ -10,9 +10,6 @@
 // cleared first by one batched zero kernel.  The tile size and block shape come
 // from ph_batch_autotune, which times candidate configurations on the bound
 // problems; the two launches can be instantiated once as a CUDA graph.
-// ph_batch_set_variant switches the batch to the double-word element code
-// (ph_assemble_dw and ph_recover_factored_dw on the fp64 record), with the same
-// bit-for-bit guarantee against those entry points.
 #include <math.h>
 #include <string.h>
 
@@ -56,70 +53,45 @@ struct Tile {
   int64_t start;
 };
 
-// MODE: 0 the fp64 element code (ph_assemble), 1 the double-word condensation
-// kernel on the fp64 record (ph_assemble_dw on such a mesh)
-template <bool UD, bool GN, bool FAC, int MODE>
+template <bool UD, bool GN, bool FAC>
 __device__ __forceinline__ void run_tile(const ProbDesc& d, int64_t start, int count) {
   for (int i = threadIdx.x; i < count; i += blockDim.x)
-    assemble_element<UD, GN, FAC, MODE>(start + i, d.geo, d.tface, d.tmult, d.tpos, d.trel, d.area, d.a, d.c20,
-                                        d.six_over_c, d.f, d.uD, d.gN, d.values, d.rhs, d.factor, d.status);
-}
-
-template <int MODE>
-__device__ __forceinline__ void batch_assemble(const ProbDesc* __restrict__ probs, const Tile* __restrict__ tiles,
-                                               int64_t ntiles) {
-  for (int64_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
-    const Tile tl = tiles[k];
-    const ProbDesc& d = probs[tl.prob];
-    switch (d.flags) {  // uniform across the block
-      case 0: run_tile<false, false, false, MODE>(d, tl.start, tl.count); break;
-      case 1: run_tile<true, false, false, MODE>(d, tl.start, tl.count); break;
-      case 2: run_tile<false, true, false, MODE>(d, tl.start, tl.count); break;
-      case 3: run_tile<true, true, false, MODE>(d, tl.start, tl.count); break;
-      case 4: run_tile<false, false, true, MODE>(d, tl.start, tl.count); break;
-      case 5: run_tile<true, false, true, MODE>(d, tl.start, tl.count); break;
-      case 6: run_tile<false, true, true, MODE>(d, tl.start, tl.count); break;
-      default: run_tile<true, true, true, MODE>(d, tl.start, tl.count); break;
-    }
-  }
+    assemble_element<UD, GN, FAC>(start + i, d.geo, d.tface, d.tmult, d.tpos, d.trel, d.area, d.a, d.c20,
+                                  d.six_over_c, d.f, d.uD, d.gN, d.values, d.rhs, d.factor, d.status);
 }
 
 // persistent: block b takes tiles b, b + gridDim.x, ...
 __global__ void k_batch_assemble(const ProbDesc* __restrict__ probs, const Tile* __restrict__ tiles, int64_t ntiles) {
-  batch_assemble<0>(probs, tiles, ntiles);
-}
-
-// the double-word variant (blocks of at most 128 threads)
-__global__ void __launch_bounds__(128) k_batch_assemble_dw(const ProbDesc* __restrict__ probs,
-                                                           const Tile* __restrict__ tiles, int64_t ntiles) {
-  batch_assemble<1>(probs, tiles, ntiles);
+  for (int64_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
+    const Tile tl = tiles[k];
+    const ProbDesc& d = probs[tl.prob];
+    switch (d.flags) {  // uniform across the block
+      case 0: run_tile<false, false, false>(d, tl.start, tl.count); break;
+      case 1: run_tile<true, false, false>(d, tl.start, tl.count); break;
+      case 2: run_tile<false, true, false>(d, tl.start, tl.count); break;
+      case 3: run_tile<true, true, false>(d, tl.start, tl.count); break;
+      case 4: run_tile<false, false, true>(d, tl.start, tl.count); break;
+      case 5: run_tile<true, false, true>(d, tl.start, tl.count); break;
+      case 6: run_tile<false, true, true>(d, tl.start, tl.count); break;
+      default: run_tile<true, true, true>(d, tl.start, tl.count); break;
+    }
+  }
 }
 
 // persistent recovery from the element factor: the same tiles, each problem's
-// elements through the plain path's per-element code (recover_element_factored,
-// or recover_element_factored_dw for the double-word variant)
-template <bool DW>
+// elements through the plain path's per-element code (recover_element_factored)
 __global__ void k_batch_recover(const ProbDesc* __restrict__ probs, const Tile* __restrict__ tiles, int64_t ntiles) {
   for (int64_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
     const Tile tl = tiles[k];
     const ProbDesc& d = probs[tl.prob];
     if (!d.u) continue;
     for (int i = threadIdx.x; i < tl.count; i += blockDim.x) {
-      if (DW) {
-        if (d.flags & 2)
-          recover_element_factored_dw<true>(tl.start + i, d.geo, d.tface, d.tmult, d.area, d.factor, d.six_over_c,
-                                            d.f, d.gN, d.lambda, d.u);
-        else
-          recover_element_factored_dw<false>(tl.start + i, d.geo, d.tface, d.tmult, d.area, d.factor, d.six_over_c,
-                                             d.f, d.gN, d.lambda, d.u);
-      } else {
-        if (d.flags & 2)
-          recover_element_factored<true>(tl.start + i, d.geo, d.tface, d.tmult, d.area, d.factor, d.six_over_c,
-                                         d.f, d.gN, d.lambda, d.u);
-        else
-          recover_element_factored<false>(tl.start + i, d.geo, d.tface, d.tmult, d.area, d.factor, d.six_over_c,
-                                          d.f, d.gN, d.lambda, d.u);
-      }
+      if (d.flags & 2)
+        recover_element_factored<true>(tl.start + i, d.geo, d.tface, d.tmult, d.area, d.factor, d.six_over_c, d.f,
+                                       d.gN, d.lambda, d.u);
+      else
+        recover_element_factored<false>(tl.start + i, d.geo, d.tface, d.tmult, d.area, d.factor, d.six_over_c, d.f,
+                                        d.gN, d.lambda, d.u);
     }
   }
 }
@@ -154,7 +126,7 @@ struct ph_batch {
   Tile* d_tiles;
   int64_t ntiles;
   int32_t tile, threads, blocks_per_sm, sms;
-  bool bound, recover, dw;  // dw: the double-word variant (ph_batch_set_variant)
+  bool bound, recover;
   cudaGraph_t graph;
   cudaGraphExec_t exec;
 };
@@ -209,7 +181,6 @@ extern "C" ph_status ph_batch_create(ph_mesh* const* meshes, int32_t n, void* st
   b->exec = nullptr;
   b->bound = false;
   b->recover = false;
-  b->dw = false;
   b->tile = 1024;
   b->threads = 128;
   b->blocks_per_sm = 4;
@@ -310,13 +281,10 @@ static cudaError_t launch_batch(ph_batch* b, cudaStream_t s) {
   }
   if (b->ntiles > 0) {
     const unsigned grid = (unsigned)std::min<int64_t>(b->ntiles, (int64_t)b->sms * b->blocks_per_sm);
-    const int threads = b->dw ? std::min(b->threads, 128) : b->threads;  // the variant's launch bound
-    if (b->dw) k_batch_assemble_dw<<<grid, threads, 0, s>>>(b->d_probs, b->d_tiles, b->ntiles);
-    else k_batch_assemble<<<grid, threads, 0, s>>>(b->d_probs, b->d_tiles, b->ntiles);
+    k_batch_assemble<<<grid, b->threads, 0, s>>>(b->d_probs, b->d_tiles, b->ntiles);
     cudaError_t e = launched();
     if (e != cudaSuccess || !b->recover) return e;
-    if (b->dw) k_batch_recover<true><<<grid, threads, 0, s>>>(b->d_probs, b->d_tiles, b->ntiles);
-    else k_batch_recover<false><<<grid, threads, 0, s>>>(b->d_probs, b->d_tiles, b->ntiles);
+    k_batch_recover<<<grid, b->threads, 0, s>>>(b->d_probs, b->d_tiles, b->ntiles);
     return launched();
   }
   return cudaSuccess;
@@ -448,12 +416,5 @@ extern "C" ph_status ph_batch_bind_recovery(ph_batch* b, const double* const* la
   if (e != cudaSuccess) return cuda_status(e, "ph_batch_bind_recovery");
   if (on != b->recover) drop_graph(b);  // the graph gains or loses the recovery launch
   b->recover = on;
-  return PH_OK;
-}
-
-extern "C" ph_status ph_batch_set_variant(ph_batch* b, int32_t variant) {
-  if (!b || variant < 0 || variant > 1) return PH_ERR_ARG;
-  if ((variant == 1) != b->dw) drop_graph(b);  // the graph holds the other kernels
-  b->dw = variant == 1;
   return PH_OK;
 }

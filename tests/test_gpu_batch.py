@@ -203,38 +203,3 @@ def test_batched_recovery_in_the_graph(ph):
     torch.cuda.synchronize()
     assert ph.ph_launch_count() - n0 == 2
     b.close()
-
-
-def test_batched_double_word_variant(ph):
-    """ph_batch_set_variant(1): every problem of the uneven batch (Neumann and
-    Dirichlet data included) bit-identical to ph_assemble_dw and
-    ph_recover_factored_dw on its mesh, under two configurations and through
-    the graph (rebuilt when the variant changes); back to fp64 afterwards."""
-    probs = problems()
-    cases = [Case(ph, p) for p in probs]
-    refs = [c.mesh.assemble(c.a, c.c, c.f, c.uD, c.gN, factor=True, variant="dw") for c in cases]
-    b = ph.Batch([c.mesh for c in cases])
-    b.bind([c.a for c in cases], [c.c for c in cases], [c.f for c in cases], [c.values for c in cases],
-           [c.rhs for c in cases], factor=[c.factor for c in cases], uD_face=[c.uD for c in cases],
-           gN_face=[c.gN for c in cases])
-    rng = np.random.default_rng(22)
-    lam = [cu(rng.standard_normal(c.mesh.L)) for c in cases]
-    us = [torch.full((c.mesh.nE, 4), np.nan, dtype=torch.float64, device="cuda") for c in cases]
-    b.bind_recovery(lam, us)
-    b.set_variant("dw")
-    for cfg in [(1024, 128, 4), (256, 256, 2)]:  # 256 threads run as 128 in the variant
-        b.set_config(*cfg)
-        _reset(cases)
-        for u in us:
-            u.fill_(np.nan)
-        b.graph_launch()
-        torch.cuda.synchronize()
-        for c, (v, r, fa), l, u in zip(cases, refs, lam, us):
-            assert torch.equal(c.values, v) and torch.equal(c.rhs, r) and torch.equal(c.factor, fa)
-            assert torch.equal(u, c.mesh.recover_factored(fa, c.c, c.f, l, c.gN, variant="dw"))
-    b.set_variant("f64")
-    _reset(cases)
-    b.assemble()
-    assert_identical(cases)
-    assert ph.load().ph_batch_set_variant(b._h, 2) == 1  # PH_ERR_ARG
-    b.close()
